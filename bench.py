@@ -1,0 +1,294 @@
+"""Benchmark: HH Metropolis site-updates/s of the GB300 sampler.
+
+Workload: Hodgkin-Huxley D = 4, all 7 parameters free, M = 32768 time steps
+(dt = 0.02 ms), seeded OU drive, noisy voltage observations.  One step is one
+full checkerboard sweep: even sites, odd sites, 7 sequential parameter moves
+(each a full-path RK4 pass plus an FP64 reduction and accept test) and, every
+N_skip = 10 sweeps, the moment/histogram update.  value = (M + 1) site updates
+per sweep / device time per sweep, summed over ranks (independent replica
+chains, weak scaling).  The L2 is flushed (a 256 MiB write) before every timed
+sweep; each sweep is timed with CUDA events on the sampler's stream.
+
+--impl reference times the serial FP64 CPU oracle (the method's plain
+statement) on the host for the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HH Metropolis site-updates/s (M=32768, 7 free params, checkerboard sweep)"
+UNIT = "site-updates/s"
+M_DEFAULT = 32768
+NSKIP = 10
+SEED = 1
+
+# Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
+# form, counted from the formula (4 field evaluations + stage combinations):
+# FP32 instructions and SFU (MUFU) operations.
+FP32_OPS_PER_MAP = 232
+MUFU_OPS_PER_MAP = 36
+# FP32 floating-point operations per map (an FMA counted as 2).
+FLOP_PER_MAP = 300
+
+
+def maps_per_sweep(M, n_free):
+    # one map per site move (sites 0..M-1 have a successor) and M per free parameter
+    return M * (1 + n_free)
+
+
+def gpu_clock_sampler(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-i", str(out["index"])]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0 and r.stdout.strip():
+                out["rows"].append([c.strip() for c in r.stdout.strip().split(",")])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def summarize_clocks(rows):
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+    mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 4 + i and r[4 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    """The serial FP64 oracle as it stands, on one host core, for a bounded
+    number of full sweeps of the same workload."""
+    import oracle
+    ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_data(prob.y, prob.I)
+    ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+    ch.set_steps(prob.sig_x, prob.sig_p)
+    ch.set_schedule(n_init=0, n_skip=NSKIP)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        ch.sweep(1, SEED)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 200:
+            break
+    return {"value": (prob.M + 1) * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full sweeps of the M={prob.M} workload (all 7 params free), serial FP64, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1103_4887_gb300 import synth
+    import oracle
+    prob = synth.hh_problem(args.M, data_seed=0, free="all")
+    ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_data(prob.y, prob.I)
+    ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+    ch.set_steps(prob.sig_x, prob.sig_p)
+    ch.set_schedule(n_init=args.warmup, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
+    for _ in range(args.warmup):
+        ch.sweep(1, SEED)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ch.sweep(1, SEED)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = (prob.M + 1) * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": 7,
+                                            "sweeps_per_step": 1, "l2": "host"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full sweeps, serial FP64 oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32mixed", choices=["fp32mixed", "fp64"])
+    ap.add_argument("--M", type=int, default=M_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=40)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1103_4887_gb300 import pimc, synth
+    prec = pimc.FP32_MIXED if args.precision == "fp32mixed" else pimc.FP64
+    prob = synth.hh_problem(args.M, data_seed=rank, free="all")
+    n_free = int(prob.free.sum())
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        s = pimc.Sampler.from_problem(prob, precision=precision)
+        s.set_stream(stream.cuda_stream)
+        s.set_chain(rank)
+        s.set_schedule(n_init=args.warmup, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
+        return s
+
+    samp = make(prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(s, K, warm):
+        for _ in range(warm):
+            s.sweep(1, SEED, sync=False)
+        torch.cuda.synchronize()
+        s.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            s.sweep(1, SEED, sync=False)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        s.sync()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    # clocks during the timed region
+    clk = {"index": local, "rows": []}
+    stop = threading.Event()
+    th = threading.Thread(target=gpu_clock_sampler, args=(stop, clk), daemon=True)
+    th.start()
+    ms = timed_steps(samp, args.steps, args.warmup)
+    stop.set()
+    th.join(timeout=10)
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sites = prob.M + 1
+    value = world * sites * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # steady state: one persistent launch of many sweeps, no flush in between
+    n_ss = 2000 if prec == pimc.FP32_MIXED else 100
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    samp.sweep(n_ss, SEED, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    samp.sync()
+    ss_ms = e0.elapsed_time(e1)
+    steady = {"sweeps_per_launch": n_ss, "ms_per_sweep": ss_ms / n_ss,
+              "site_updates_per_s": world * sites * n_ss / (ss_ms * 1e-3)}
+
+    # e2e through the public API with host buffers: per step the data arrays
+    # go host->device from pinned memory (pimc_load_data), one sweep runs, and
+    # the parameter vector comes back (pimc_get_state)
+    y_pin = torch.from_numpy(prob.y.copy()).pin_memory()
+    I_pin = torch.from_numpy(prob.I.copy()).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samp.load_data(y_pin.data_ptr(), I_pin.data_ptr())
+        samp.sweep(1, SEED, sync=False)
+        p_now = samp.params()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * sites * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (2 * prob.M + 1), "d2h_bytes_per_step": 8 * 7}
+
+    # FP64 form on the same workload (for the FP32-mixed vs FP64 comparison)
+    fp64 = None
+    if prec == pimc.FP32_MIXED and args.fp64_steps > 0:
+        s64 = make(pimc.FP64)
+        ms64 = timed_steps(s64, args.fp64_steps, 3)
+        fp64 = {"value": world * sites * args.fp64_steps / (sum(ms64) * 1e-3), "ms_per_step": sum(ms64) / len(ms64)}
+        s64.close()
+
+    peaks, peak_src = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    maps = maps_per_sweep(args.M, n_free)
+    if prec == pimc.FP32_MIXED:
+        # compute roofline of the map's instruction mix: FP32 lanes 128/clk/SM,
+        # SFU 16/clk/SM at the maximum SM clock
+        t_map = max(FP32_OPS_PER_MAP / (n_sm * 128 * sm_mhz * 1e6), MUFU_OPS_PER_MAP / (n_sm * 16 * sm_mhz * 1e6))
+        peak_tflops = FLOP_PER_MAP / t_map / 1e12
+    else:
+        peak_tflops = 1.25  # nominal FP64 rate of the part
+    achieved = maps * FLOP_PER_MAP / (ms_per_step * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
+            "kernel": "sweep_kernel<HH>", "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if prec == pimc.FP32_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": n_free,
+                           "precision": args.precision, "sweeps_per_step": 1, "n_skip": NSKIP,
+                           "l2": "flushed (256 MiB write) before every timed sweep",
+                           "grid_block": list(samp.launch_info())},
+                "gpu_launches": args.steps,
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk["rows"]),
+                "steady_state": steady, "fp64": fp64}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

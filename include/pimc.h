@@ -1,0 +1,206 @@
+/*
+ * pimc.h -- C ABI of the GB300 (sm_103a) path-integral Monte Carlo sampler
+ * for data assimilation (Quinn & Abarbanel, "Data Assimilation using a GPU
+ * Accelerated Path Integral Monte Carlo Approach").
+ *
+ * The sampler draws paths X = {x_0..x_M} (x_n in R^D, SoA layout
+ * X[a*(M+1)+n]) and parameters p (N_p of them) from P(X|Y) ~ exp(-A):
+ *
+ *   A = 1/2 Rm sum_{n=1}^{M} (x_{n,0} - y_n)^2                       (A_o)
+ *     + beta/2 sum_{n=0}^{M-1} sum_a Rf_a (x_{n+1,a} - f_a(x_n,p;I_n))^2  (A_f)
+ *
+ * -- Eq. (action) under the Gaussian measurement/model-error assumptions of
+ * Sec. 2.1 (Eq. (obsError), Eq. (modelError)), with the model-error residual
+ * taken against an explicit one-step RK4 map f of the model vector field and
+ * beta the annealing multiplier of Sec. 4.2.  The observation function is
+ * h(x) = x_0 (L = 1, Sec. 5.1).  A uniform prior box on p (Sec. 2.1, last
+ * assumption; Sec. 4.2, "boundaries on parameters") rejects out-of-box moves.
+ *
+ * Conventions
+ *   * Every function returns PIMC_OK (0) or a negative pimc_status.  The text
+ *     of the last error of a handle is pimc_last_error(h).
+ *   * A handle owns all of its device buffers.  Host arrays passed in are
+ *     caller-owned and copied; host arrays passed out are caller-allocated
+ *     and filled.  Functions taking *_dev pointers use caller-owned device
+ *     memory and never free it.
+ *   * Work is enqueued on the handle's stream (pimc_set_stream; default: a
+ *     stream the handle creates).  pimc_sweep returns once its kernels are
+ *     enqueued; functions that return host data synchronise the stream and
+ *     report any error flagged by a kernel (e.g. PIMC_ERR_TIMEOUT).
+ *   * A handle is not thread-safe; separate handles are independent.
+ *   * Sizes: M >= 1; D and N_p are fixed by the model (HH: D = 4, N_p = 7;
+ *     LINGAUSS: D = 2, N_p = 1; TOY1D: D = 1, N_p = 1).
+ */
+#ifndef PIMC_H
+#define PIMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pimc_handle_s* pimc_t;
+
+typedef enum {
+    PIMC_OK = 0,
+    PIMC_ERR_ARG = -1,      /* invalid argument (size, pointer, non-finite value) */
+    PIMC_ERR_STATE = -2,    /* call out of order (e.g. sweep before set_data) */
+    PIMC_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    PIMC_ERR_OOM = -4,      /* device allocation failed */
+    PIMC_ERR_TIMEOUT = -5,  /* a bounded device-side wait expired; the launch returned early */
+    PIMC_ERR_NUMERIC = -6,  /* non-finite value where a finite one is required */
+    PIMC_ERR_IO = -7        /* checkpoint file missing, short or corrupt */
+} pimc_status;
+
+typedef enum {
+    PIMC_MODEL_HH = 0,       /* Hodgkin-Huxley, x = (V, m, h, n),
+                                p = (gNa, gK, gL, ENa, EK, EL, C) (Sec. 5.1) */
+    PIMC_MODEL_LINGAUSS = 1, /* dx/dt = K x + (p0, I), K = [[-0.5,-2],[2,-0.5]] (test model) */
+    PIMC_MODEL_TOY1D = 2     /* dx/dt = p0 sin(x) - x/2 + I (test model) */
+} pimc_model;
+
+typedef enum {
+    PIMC_FP64 = 0,           /* every step in FP64 */
+    PIMC_FP32_MIXED = 1      /* path, cache and per-site arithmetic in FP32; the
+                                parameter-move reduction, its accept test, the
+                                global action and the moment sums in FP64 */
+} pimc_precision;
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/* Create a sampler for `model` over sites n = 0..M with time step dt.
+ * L must be 1 and D must equal the model's dimension.  Rm points to one
+ * double (the measurement precision R_o of Eq. (obsError), > 0); Rf to D
+ * doubles (the diagonal model-error precision R_d of Eq. (modelError), >= 0).
+ * The device is the CUDA device current on the calling thread.
+ * Errors: PIMC_ERR_ARG (bad sizes/values), PIMC_ERR_OOM, PIMC_ERR_CUDA. */
+int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt,
+                const double* Rm, const double* Rf);
+int pimc_destroy(pimc_t h);
+const char* pimc_last_error(pimc_t h);
+/* Use `stream` (a cudaStream_t, may be NULL for the legacy default stream)
+ * for all further work of this handle.  The caller keeps ownership. */
+int pimc_set_stream(pimc_t h, void* stream);
+/* Select the arithmetic (pimc_precision).  Re-initialises the path from its
+ * current FP64 value; call before pimc_sweep. */
+int pimc_set_precision(pimc_t h, int precision);
+
+/* ---- problem data (Sec. 4.1, "the current path, the observation time series,
+ *      the external drive signal ... are allocated in GPU memory") ---------- */
+
+/* y: M+1 observations (y_0 only seeds the initial path); I_inj: M drive values,
+ * held over [t_n, t_{n+1}).  Both must be finite.  Re-initialises the path to
+ * the default initial guess: x_{n,0} = y_n, other components at the model's
+ * steady state for that voltage (HH gates a_inf = alpha/(alpha+beta)). */
+int pimc_set_data(pimc_t h, const double* y, const double* I_inj);
+/* Replace y and I_inj without re-initialising the path (new data for a running
+ * chain, e.g. the next observation window); refreshes the f cache.  Enqueued
+ * on the handle's stream: with pinned host arrays the copies are asynchronous
+ * and the arrays must stay unchanged until the next synchronising call. */
+int pimc_load_data(pimc_t h, const double* y, const double* I_inj);
+/* p, lo, hi: Np doubles; free_mask: Np bytes (1 = sampled, 0 = fixed).
+ * lo <= p <= hi is required for free parameters. */
+int pimc_set_params(pimc_t h, const double* p, const double* lo, const double* hi,
+                    const uint8_t* free_mask, int Np);
+/* Optional explicit path, D*(M+1) doubles in SoA layout. */
+int pimc_set_path(pimc_t h, const double* X);
+/* Proposal scales: sigma_x has D doubles (same for every site) when
+ * per_site == 0, or D*(M+1) doubles when per_site == 1; sigma_p has Np doubles. */
+int pimc_set_steps(pimc_t h, const double* sigma_x, int per_site, const double* sigma_p);
+/* Burn-in and recording schedule (Sec. 4.1-4.2): statistics are recorded at
+ * sweeps s >= n_init with (s - n_init) % n_skip == 0; during s < n_init the
+ * proposal scales are adapted every n_skip sweeps by
+ * sigma <- sigma [1 + alpha (N_acc/n_skip - f_acc)]; beta starts at beta0 and
+ * is multiplied by f_beta = (1/beta0)^(1/n_cool) after each sweep until
+ * sweep n_cool, then stays 1 (Eq. (fbeta)).  Requires n_skip >= 1,
+ * 0 < beta0 <= 1.  Resets the sweep counter to 0 and clears the statistics. */
+int pimc_set_schedule(pimc_t h, int64_t n_init, int64_t n_skip, double beta0, int64_t n_cool,
+                      double f_acc, double alpha);
+/* Chain index (fourth Philox counter word); distinct chains on the same data
+ * and seed draw independent streams. */
+int pimc_set_chain(pimc_t h, uint32_t chain);
+
+/* ---- the hot path ---------------------------------------------------------- */
+
+/* Run n_sweeps checkerboard sweeps (Fig. 1, Sec. 4.1): even sites, then odd
+ * sites, then each free parameter in order, then (when due) the statistics,
+ * the step adaptation and the annealing step.  Random numbers are
+ * Philox-4x32-10 keyed by `seed` with counters (n or l, sweep, kind, chain),
+ * so a run resumes exactly at the handle's sweep counter.  Asynchronous. */
+int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed);
+/* Synchronise and return the sticky device status (PIMC_ERR_TIMEOUT if a
+ * bounded wait expired in any launch since the last call; the flag is cleared). */
+int pimc_sync(pimc_t h);
+
+/* Full action of the current state at beta = 1: A = A_o + A_f (Sec. 2.1). */
+int pimc_action(pimc_t h, double* A_out, double* Ao_out, double* Af_out);
+/* Gradient of A_o + beta A_f with respect to X (D*(M+1) doubles, SoA) and p
+ * (Np doubles; entries of fixed parameters are still filled). */
+int pimc_grad(pimc_t h, double beta, double* gX, double* gp);
+
+/* Action and gradient of caller-owned device arrays against this handle's
+ * data and settings (for autograd / HMC drivers).  X_dev: D*(M+1) doubles,
+ * p_dev: Np doubles, out_dev: 3 doubles (A, A_o, A_f at beta = 1);
+ * gX_dev: D*(M+1), gp_dev: Np doubles.  Enqueued on `stream`; no sync. */
+int pimc_action_dev(pimc_t h, const double* X_dev, const double* p_dev, double* out_dev,
+                    void* stream);
+int pimc_grad_dev(pimc_t h, const double* X_dev, const double* p_dev, double beta,
+                  double* gX_dev, double* gp_dev, void* stream);
+
+/* ---- diagnostics of the hot path (parity tests) ------------------------------ */
+
+/* Local change of action Delta A_n for replacing x_n by Xp[:,n], each site
+ * against the current path (Fig. 1 steps (b)-(g)), for all n = 0..M. */
+int pimc_site_delta(pimc_t h, const double* Xp, double beta, double* dA_out);
+/* Change of action for moving parameter l to pl_new over the whole path. */
+int pimc_param_delta(pimc_t h, int l, double pl_new, double beta, double* dA_out);
+
+/* ---- statistics (Sec. 4.1, "path statistics ... on the GPU") --------------- */
+
+/* mean, var: D*(M+1)+Np doubles each (path components in SoA order, then p);
+ * var is the unbiased sample variance.  n_samples may be NULL. */
+int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples);
+/* Histograms of n_sel components (index c < D*(M+1) selects X[c], otherwise
+ * p[c - D*(M+1)]): n_bins equal bins on [lo, hi) plus under/overflow slots.
+ * 1 <= n_sel <= 64, 1 <= n_bins <= 4096.  Clears the counts. */
+int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const double* lo,
+                        const double* hi, int n_bins);
+/* counts: n_sel*(n_bins+2) uint64, per component [under, bins..., over]. */
+int pimc_histograms(pimc_t h, uint64_t* counts);
+/* Current histogram configuration (0, 0 when none is set). */
+int pimc_histogram_shape(pimc_t h, int* n_sel, int* n_bins);
+
+/* ---- state ----------------------------------------------------------------- */
+int pimc_get_state(pimc_t h, double* X, double* p);
+int pimc_get_steps(pimc_t h, double* sigma_x /*D*(M+1)*/, double* sigma_p /*Np*/);
+/* Current sweep counter and beta. */
+int pimc_get_sweep(pimc_t h, int64_t* sweep, double* beta);
+/* Totals since the last pimc_set_schedule: accepted and proposed site moves
+ * (index 0 even, 1 odd), accepted and proposed parameter moves (Np each). */
+int pimc_accept_stats(pimc_t h, uint64_t* site_acc, uint64_t* site_prop, uint64_t* par_acc,
+                      uint64_t* par_prop);
+/* Launch geometry chosen for the sweep kernel (grid CTAs, threads per CTA). */
+int pimc_launch_info(pimc_t h, int* grid, int* block);
+
+/* ---- checkpoint / resume ------------------------------------------------------ */
+/* Binary file with a version and a CRC: sizes, settings, path, p, steps,
+ * schedule position, statistics and counters.  Resuming and continuing gives
+ * bit-identical results to an uninterrupted run (counter-based RNG). */
+int pimc_checkpoint_save(pimc_t h, const char* path);
+int pimc_checkpoint_load(pimc_t h, const char* path);
+
+/* ---- test hooks ---------------------------------------------------------------- */
+/* Bounded-wait limit of the grid barrier in nanoseconds (default 2e9). */
+int pimc_set_wait_limit(pimc_t h, int64_t ns);
+/* Make CTA `cta` skip its barrier arrivals in later sweeps (-1: off), so the
+ * other CTAs' bounded waits expire and pimc_sync reports PIMC_ERR_TIMEOUT. */
+int pimc_debug_skip_arrive(pimc_t h, int cta);
+/* Force the sweep grid size (0: automatic). */
+int pimc_set_grid(pimc_t h, int grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIMC_H */

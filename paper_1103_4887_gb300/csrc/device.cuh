@@ -1,0 +1,316 @@
+// Device building blocks of the sampler: counter-based RNG, model vector
+// fields with their transposed Jacobian products, the RK4 map and its reverse
+// mode, and the per-site / per-parameter changes of action.  Templated on the
+// arithmetic type R (double for PIMC_FP64, float for PIMC_FP32_MIXED).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pimc {
+
+constexpr int kMaxD = 4;
+constexpr int kMaxP = 8;
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products whose high words are xored with the other counter
+// words and the round key; the key advances by the Weyl increments.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t ha = __umulhi(0xD2511F53u, c.x), la = 0xD2511F53u * c.x;
+        const uint32_t hb = __umulhi(0xCD9E8D57u, c.z), lb = 0xCD9E8D57u * c.z;
+        c = make_uint4(hb ^ c.y ^ k0, lb, ha ^ c.w ^ k1, la);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum : uint32_t { kKindSite = 0, kKindParam = 1, kKindHmcMom = 2, kKindHmcAcc = 3 };
+
+__device__ __forceinline__ uint4 draw_block(uint64_t seed, uint32_t chain, uint64_t sweep,
+                                            uint32_t idx, uint32_t kind, uint32_t blk)
+{
+    return philox(make_uint4(idx, (uint32_t)sweep, (kind << 24) | blk, chain),
+                  (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Open-interval uniforms.  FP64: 52-bit integer from the top 26 bits of two
+// words, (k + 1/2) 2^-52.  FP32: top 24 bits of one word, (k + 1/2) 2^-24
+// (the same high bits as the FP64 form, so both precisions see nearly the
+// same number).
+__device__ __forceinline__ double u01d(uint32_t hi, uint32_t lo)
+{
+    const uint64_t k = ((uint64_t)(hi >> 6) << 26) | (uint64_t)(lo >> 6);
+    return ((double)k + 0.5) * 0x1.0p-52;
+}
+__device__ __forceinline__ float u01f(uint32_t hi) { return ((float)(hi >> 8) + 0.5f) * 0x1.0p-24f; }
+
+template <class R> struct Num;
+
+template <> struct Num<double> {
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double uni(uint32_t hi, uint32_t lo) { return u01d(hi, lo); }
+    // Box-Muller: r cos(2 pi u2), r sin(2 pi u2), r = sqrt(-2 log u1)
+    static __device__ __forceinline__ void box_muller(uint4 w, double& z0, double& z1)
+    {
+        const double r = sqrt(-2.0 * log(u01d(w.x, w.y)));
+        double s, c;
+        sincospi(2.0 * u01d(w.z, w.w), &s, &c);
+        z0 = r * c;
+        z1 = r * s;
+    }
+    static constexpr double psi_cut = 1e-6;
+    static constexpr double dpsi_cut = 1e-3;
+};
+
+template <> struct Num<float> {
+    // SFU exponential (ex2.approx) and reciprocal for the per-site arithmetic
+    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+    static __device__ __forceinline__ float exm1(float x) { return __expf(x) - 1.0f; }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float uni(uint32_t hi, uint32_t) { return u01f(hi); }
+    static __device__ __forceinline__ void box_muller(uint4 w, float& z0, float& z1)
+    {
+        const float r = sqrtf(-2.0f * __logf(u01f(w.x)));
+        float s, c;
+        __sincosf(6.283185307179586f * u01f(w.z), &s, &c);
+        z0 = r * c;
+        z1 = r * s;
+    }
+    static constexpr float psi_cut = 1e-2f;
+    static constexpr float dpsi_cut = 1e-1f;
+};
+
+// ---------------------------------------------------------------------------
+// Models.  Parameters arrive as R p[kMaxP].
+// ---------------------------------------------------------------------------
+
+// u / (1 - e^{-u}): the alpha_m / alpha_n form; its removable singularity at
+// u = 0 is replaced by the series 1 + u/2 + u^2/12 below the cut.
+template <class R> __device__ __forceinline__ R psi(R u)
+{
+    if (fabs(u) < Num<R>::psi_cut) return R(1) + u * (R(0.5) + u * R(1.0 / 12.0));
+    return Num<R>::div(-u, Num<R>::exm1(-u));
+}
+// d psi/du = (1 - e^{-u} - u e^{-u}) / (1 - e^{-u})^2; series
+// 1/2 + u/6 - u^3/180 + u^5/5040 below the cut.
+template <class R> __device__ __forceinline__ R dpsi(R u)
+{
+    if (fabs(u) < Num<R>::dpsi_cut) {
+        const R u2 = u * u;
+        return R(0.5) + u * (R(1.0 / 6.0) + u2 * (R(-1.0 / 180.0) + u2 * R(1.0 / 5040.0)));
+    }
+    const R em = -Num<R>::exm1(-u);
+    const R e = Num<R>::ex(-u);
+    return Num<R>::div(em - u * e, em * em);
+}
+
+// Hodgkin-Huxley (1952) in the modern convention, conductance form:
+//   C dV/dt = I - gNa m^3 h (V - ENa) - gK n^4 (V - EK) - gL (V - EL)
+//   da/dt = alpha_a(V)(1 - a) - beta_a(V) a          (Sec. 5.1, Eq. (dadt) structure)
+// p = (gNa, gK, gL, ENa, EK, EL, C).
+template <class R> struct HH {
+    static constexpr int D = 4, NP = 7;
+    // q = (gNa, gK, gL, ENa, EK, EL, C, 1/C): the reciprocal capacitance is
+    // formed once per parameter value instead of once per vector-field call.
+    static __device__ __forceinline__ void prep(const double* p, R* q)
+    {
+#pragma unroll
+        for (int l = 0; l < NP; ++l) q[l] = R(p[l]);
+        q[7] = R(1.0 / p[6]);
+    }
+    // Rates in 1/ms, V in mV; divisions by constants written as products.
+    static __device__ __forceinline__ void rates(R V, R a[3], R b[3])
+    {
+        a[0] = psi<R>((V + R(40)) * R(0.1));
+        b[0] = R(4) * Num<R>::ex((V + R(65)) * R(-1.0 / 18.0));
+        a[1] = R(0.07) * Num<R>::ex((V + R(65)) * R(-0.05));
+        b[1] = Num<R>::div(R(1), R(1) + Num<R>::ex((V + R(35)) * R(-0.1)));
+        a[2] = R(0.1) * psi<R>((V + R(55)) * R(0.1));
+        b[2] = R(0.125) * Num<R>::ex((V + R(65)) * R(-0.0125));
+    }
+    static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F)
+    {
+        R a[3], b[3];
+        rates(x[0], a, b);
+        const R V = x[0], m = x[1], h = x[2], n = x[3];
+        const R iNa = q[0] * m * m * m * h * (V - q[3]);
+        const R iK = q[1] * n * n * n * n * (V - q[4]);
+        const R iL = q[2] * (V - q[5]);
+        F[0] = (I - iNa - iK - iL) * q[7];
+        F[1] = a[0] * (R(1) - m) - b[0] * m;
+        F[2] = a[1] * (R(1) - h) - b[1] * h;
+        F[3] = a[2] * (R(1) - n) - b[2] * n;
+    }
+    // gx += J_x^T w, gp += J_p^T w (gp indexed like p: 7 entries)
+    static __device__ __forceinline__ void rhs_vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp)
+    {
+        R a[3], b[3];
+        rates(x[0], a, b);
+        const R V = x[0], m = x[1], h = x[2], n = x[3];
+        R da[3], db[3];
+        da[0] = dpsi<R>((V + R(40)) * R(0.1)) * R(0.1);
+        db[0] = b[0] * R(-1.0 / 18.0);
+        da[1] = a[1] * R(-0.05);
+        db[1] = b[1] * (R(1) - b[1]) * R(0.1);
+        da[2] = dpsi<R>((V + R(55)) * R(0.1)) * R(0.01);
+        db[2] = b[2] * R(-0.0125);
+        const R gNa = q[0], gK = q[1], gL = q[2], ENa = q[3], EK = q[4], EL = q[5], iC = q[7];
+        const R m3h = m * m * m * h, n4 = n * n * n * n;
+        const R num = I - gNa * m3h * (V - ENa) - gK * n4 * (V - EK) - gL * (V - EL);
+        const R wv = w[0] * iC;
+        gx[0] += wv * (-gNa * m3h - gK * n4 - gL);
+        gx[1] += wv * (R(-3) * gNa * m * m * h * (V - ENa));
+        gx[2] += wv * (-gNa * m * m * m * (V - ENa));
+        gx[3] += wv * (R(-4) * gK * n * n * n * (V - EK));
+        gp[0] += wv * (-m3h * (V - ENa));
+        gp[1] += wv * (-n4 * (V - EK));
+        gp[2] += wv * (-(V - EL));
+        gp[3] += wv * (gNa * m3h);
+        gp[4] += wv * (gK * n4);
+        gp[5] += wv * gL;
+        gp[6] += w[0] * (-num * iC * iC);
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            const R s = x[1 + g];
+            gx[1 + g] += w[1 + g] * (-(a[g] + b[g]));
+            gx[0] += w[1 + g] * (da[g] * (R(1) - s) - db[g] * s);
+        }
+    }
+    // default initial path: V from the observation, gates at a_inf(V)
+    static __device__ __forceinline__ void init_site(R V, R* x)
+    {
+        R a[3], b[3];
+        rates(V, a, b);
+        x[0] = V;
+        for (int g = 0; g < 3; ++g) x[1 + g] = a[g] / (a[g] + b[g]);
+    }
+};
+
+// Linear test model: dx/dt = K x + (p0, I), K = [[-0.5, -2], [2, -0.5]].
+template <class R> struct LinGauss {
+    static constexpr int D = 2, NP = 1;
+    static __device__ __forceinline__ void prep(const double* p, R* q) { q[0] = R(p[0]); }
+    static __device__ __forceinline__ void rhs(const R* x, const R* p, R I, R* F)
+    {
+        F[0] = R(-0.5) * x[0] + R(-2.0) * x[1] + p[0];
+        F[1] = R(2.0) * x[0] + R(-0.5) * x[1] + I;
+    }
+    static __device__ __forceinline__ void rhs_vjp(const R* x, const R* p, R I, const R* w, R* gx, R* gp)
+    {
+        gx[0] += R(-0.5) * w[0] + R(2.0) * w[1];
+        gx[1] += R(-2.0) * w[0] + R(-0.5) * w[1];
+        gp[0] += w[0];
+    }
+    static __device__ __forceinline__ void init_site(R V, R* x) { x[0] = V; x[1] = R(0); }
+};
+
+// Scalar test model: dx/dt = p0 sin(x) - x/2 + I.
+template <class R> struct Toy1D {
+    static constexpr int D = 1, NP = 1;
+    static __device__ __forceinline__ void prep(const double* p, R* q) { q[0] = R(p[0]); }
+    static __device__ __forceinline__ void rhs(const R* x, const R* p, R I, R* F)
+    {
+        F[0] = p[0] * sin(x[0]) - R(0.5) * x[0] + I;
+    }
+    static __device__ __forceinline__ void rhs_vjp(const R* x, const R* p, R I, const R* w, R* gx, R* gp)
+    {
+        gx[0] += w[0] * (p[0] * cos(x[0]) - R(0.5));
+        gp[0] += w[0] * sin(x[0]);
+    }
+    static __device__ __forceinline__ void init_site(R V, R* x) { x[0] = V; }
+};
+
+// One classical RK4 step of size dt with the drive held at I:
+// f = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+template <class Model, class R>
+__device__ __forceinline__ void rk4_map(const R* x, const R* p, R I, R dt, R* f)
+{
+    constexpr int D = Model::D;
+    R k[D], xs[D], acc[D];
+    Model::rhs(x, p, I, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] = k[a]; xs[a] = x[a] + R(0.5) * dt * k[a]; }
+    Model::rhs(xs, p, I, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] = acc[a] + R(2) * k[a]; xs[a] = x[a] + R(0.5) * dt * k[a]; }
+    Model::rhs(xs, p, I, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { acc[a] = acc[a] + R(2) * k[a]; xs[a] = x[a] + dt * k[a]; }
+    Model::rhs(xs, p, I, k);
+#pragma unroll
+    for (int a = 0; a < D; ++a) f[a] = x[a] + dt / R(6) * (acc[a] + k[a]);
+}
+
+// Reverse mode through the RK4 step: the stage states are recomputed from x
+// (nothing stored), then the cotangent w of f is pulled back stage by stage.
+// Also returns f itself.  gx, gp are accumulated into.
+template <class Model, class R>
+__device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, const R* w, R* f,
+                                        R* gx, R* gp)
+{
+    constexpr int D = Model::D;
+    R k1[D], k2[D], k3[D], k4[D], x2[D], x3[D], x4[D];
+    Model::rhs(x, p, I, k1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) x2[a] = x[a] + R(0.5) * dt * k1[a];
+    Model::rhs(x2, p, I, k2);
+#pragma unroll
+    for (int a = 0; a < D; ++a) x3[a] = x[a] + R(0.5) * dt * k2[a];
+    Model::rhs(x3, p, I, k3);
+#pragma unroll
+    for (int a = 0; a < D; ++a) x4[a] = x[a] + dt * k3[a];
+    Model::rhs(x4, p, I, k4);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        f[a] = x[a] + dt / R(6) * (((k1[a] + R(2) * k2[a]) + R(2) * k3[a]) + k4[a]);
+
+    R b1[D], b2[D], b3[D], b4[D], u[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        gx[a] += w[a];
+        b1[a] = dt / R(6) * w[a];
+        b2[a] = dt / R(3) * w[a];
+        b3[a] = dt / R(3) * w[a];
+        b4[a] = dt / R(6) * w[a];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = R(0);
+    Model::rhs_vjp(x4, p, I, b4, u, gp);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { gx[a] += u[a]; b3[a] += dt * u[a]; u[a] = R(0); }
+    Model::rhs_vjp(x3, p, I, b3, u, gp);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { gx[a] += u[a]; b2[a] += R(0.5) * dt * u[a]; u[a] = R(0); }
+    Model::rhs_vjp(x2, p, I, b2, u, gp);
+#pragma unroll
+    for (int a = 0; a < D; ++a) { gx[a] += u[a]; b1[a] += R(0.5) * dt * u[a]; u[a] = R(0); }
+    Model::rhs_vjp(x, p, I, b1, u, gp);
+#pragma unroll
+    for (int a = 0; a < D; ++a) gx[a] += u[a];
+}
+
+// 1/2 R (d'^2 - d^2) evaluated as 1/2 R (d' - d)(d' + d): no cancellation of
+// two large squares (the local change of action of Fig. 1, steps (e)-(f)).
+template <class R> __device__ __forceinline__ R sqdiff(R Rw, R dp, R d)
+{
+    return R(0.5) * Rw * (dp - d) * (dp + d);
+}
+
+// Metropolis rule, Eq. (Paccept): accept iff dA <= 0 or u < exp(-dA);
+// a non-finite dA is a rejection.
+template <class R> __device__ __forceinline__ bool metropolis(R dA, R u)
+{
+    if (!isfinite(dA)) return false;
+    if (dA <= R(0)) return true;
+    return u < Num<R>::ex(-dA);
+}
+
+}  // namespace pimc

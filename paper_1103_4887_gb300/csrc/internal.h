@@ -1,0 +1,81 @@
+// Internal interface between the host runtime (runtime.cu) and the kernels
+// (sweep.cu, ops.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pimc {
+
+constexpr int kBlock = 128;          // threads per CTA of every kernel
+constexpr int kMaxParams = 8;
+constexpr int kMaxGrid = 4096;       // upper bound on CTAs of a launch (partials capacity)
+constexpr int kMaxSel = 64;          // histogram components
+constexpr int kMaxBins = 4096;
+
+// Scalar sampler state living in device memory.  The sweep kernel keeps a
+// per-CTA copy in shared memory; every CTA evolves it identically (same draws,
+// same fixed-order sums) and CTA 0 writes it back at the end of a launch.
+struct DevState {
+    double p[8], lo[8], hi[8], sigp[8];
+    double beta;
+    long long sweep, J;
+    unsigned fidx, free_mask;
+    unsigned accp_win[8];
+    unsigned long long site_acc[2], site_prop[2], par_acc[8], par_prop[8], nonfinite;
+    int status;   // sticky error bits (kStatusTimeout)
+    int abort;    // set by a CTA whose bounded wait expired; all CTAs leave
+};
+
+constexpr int kStatusTimeout = 1;
+
+// Everything a kernel needs, passed by value.
+struct Ctx {
+    int64_t M, ldx, ldf;          // sites 0..M; row strides of [D][ldx] and [D][ldf] arrays
+    double dt, Rm, Rf[4];
+    void* X;                      // R[D][ldx]
+    void* F[2];                   // R[D][ldf]: cached f(x_n), double-buffered (Sec. 4.3)
+    const void* y;                // R[ldx]
+    const void* I;                // R[ldf]
+    void* sig;                    // R[D][ldx]
+    uint32_t* acc_win;            // [ldx] accepted moves per site in the adaptation window
+    DevState* st;
+    double* partials;             // [2][kMaxGrid] per-CTA parameter-move sums
+    unsigned* bar;                // [0] arrivals, [1] generation of the grid barrier
+    unsigned* ticket;             // last-block counter of single-pass reductions
+    double* red;                  // [kMaxGrid * 8] per-CTA partials of single-pass reductions
+    double *S1, *S2, *shift;      // [D*(M+1) + NP] running shifted sums (FP64)
+    unsigned long long* hist;     // [n_sel][n_bins + 2]
+    const int64_t* h_comp;
+    const double *h_lo, *h_hi;
+    int n_sel, n_bins;
+    int64_t n_init, n_skip, n_cool;
+    double fbeta, f_acc, alpha;
+    uint64_t seed;
+    uint32_t chain;
+    int64_t wait_ns;
+    int skip_cta;
+    int64_t tile;                 // sites per CTA in the sweep kernel
+};
+
+// Kernel launchers (model: pimc_model, prec: pimc_precision).
+cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s);
+int sweep_max_grid(int model, int prec, int device);  // co-resident CTAs on the device
+cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s);
+cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s);
+// out: 3 doubles (A, Ao, Af).  X_ext/p_ext: FP64 caller arrays ([D][M+1] dense, [NP]) or null
+// for the handle's own state.
+cudaError_t launch_action(int model, int prec, const Ctx& c, const double* X_ext, const double* p_ext,
+                          double* out, cudaStream_t s);
+cudaError_t launch_grad(int model, int prec, const Ctx& c, const double* X_ext, const double* p_ext,
+                        double beta, double* gX, double* gp, cudaStream_t s);
+cudaError_t launch_site_delta(int model, int prec, const Ctx& c, const double* Xp, double beta,
+                              double* dA, cudaStream_t s);
+cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double pl_new, double beta,
+                               double* out, cudaStream_t s);
+// dst[i] = (storage type) src[i], i < n.
+cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s);
+// X conversion between the handle storage and dense FP64 [D][M+1].
+cudaError_t launch_path_io(int prec, const Ctx& c, int D, double* dense, int to_state, cudaStream_t s);
+
+}  // namespace pimc

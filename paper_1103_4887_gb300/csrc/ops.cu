@@ -1,0 +1,264 @@
+// Whole-path operations outside the sweep: the default initial path, the f
+// cache refresh, the global action (FP64 sums), its gradient by reverse mode
+// through the RK4 map (stages recomputed), and path layout conversion.
+#include "device.cuh"
+#include "internal.h"
+
+namespace pimc {
+
+template <class Model, class R>
+__global__ void init_path_kernel(Ctx c)
+{
+    constexpr int D = Model::D;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > c.M) return;
+    R x[D];
+    Model::init_site(((const R*)c.y)[n], x);
+    for (int a = 0; a < D; ++a) ((R*)c.X)[a * c.ldx + n] = x[a];
+}
+
+// f_n = f(x_n, p; I_n) into the current cache buffer.
+template <class Model, class R>
+__global__ void refresh_cache_kernel(Ctx c)
+{
+    constexpr int D = Model::D;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= c.M) return;
+    R pr[kMaxP], x[D], f[D];
+    Model::prep(c.st->p, pr);
+    const R* X = (const R*)c.X;
+    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), f);
+    R* F = (R*)c.F[c.st->fidx];
+    for (int a = 0; a < D; ++a) F[a * c.ldf + n] = f[a];
+}
+
+template <class T> __device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// K FP64 sums: per-CTA fixed-order sums into c.red[cta*8+k]; the last CTA to
+// arrive adds the CTA sums in CTA order and writes out[k].  Deterministic.
+template <int K>
+__device__ void grid_sums_last_block(const Ctx& c, double (&v)[K], double* out, double (*wsum)[kBlock / 32],
+                                     int* last)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double w = warp_sum_d<double>(v[k]);
+        if (lane == 0) wsum[k][wid] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (int j = 0; j < kBlock / 32; ++j) t += wsum[k][j];
+            c.red[(int64_t)blockIdx.x * 8 + k] = t;
+        }
+        __threadfence();
+        *last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (*last && threadIdx.x == 0) {
+        __threadfence();
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(&c.red[(int64_t)i * 8 + k]);
+            out[k] = t;
+        }
+        *c.ticket = 0u;
+    }
+}
+
+// Path element (a, n) from either the handle's storage or a dense FP64 array.
+template <class R>
+__device__ __forceinline__ R path_at(const Ctx& c, const double* Xe, int a, int64_t n)
+{
+    return Xe ? R(Xe[a * (c.M + 1) + n]) : ((const R*)c.X)[a * c.ldx + n];
+}
+
+// A = A_o + A_f (beta = 1): out = (A, A_o, A_f).  Per-site residuals in R,
+// squares accumulated in FP64.
+template <class Model, class R>
+__global__ void __launch_bounds__(kBlock) action_kernel(Ctx c, const double* Xe, const double* pe, double* out)
+{
+    constexpr int D = Model::D;
+    __shared__ double wsum[2][kBlock / 32];
+    __shared__ int last;
+    __shared__ double res[2];
+    R pr[kMaxP];
+    Model::prep(pe ? pe : c.st->p, pr);
+    double v[2] = {0.0, 0.0};
+    const R* y = (const R*)c.y;
+    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n <= c.M; n += (int64_t)gridDim.x * kBlock) {
+        R x[D];
+        for (int a = 0; a < D; ++a) x[a] = path_at<R>(c, Xe, a, n);
+        if (n >= 1) {
+            const R d = x[0] - y[n];
+            v[0] += 0.5 * c.Rm * (double)d * (double)d;
+        }
+        if (n < c.M) {
+            R f[D];
+            rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), f);
+            for (int a = 0; a < D; ++a) {
+                const R e = path_at<R>(c, Xe, a, n + 1) - f[a];
+                v[1] += 0.5 * c.Rf[a] * (double)e * (double)e;
+            }
+        }
+    }
+    grid_sums_last_block<2>(c, v, res, wsum, &last);
+    if (last && threadIdx.x == 0) {
+        out[0] = res[0] + res[1];
+        out[1] = res[0];
+        out[2] = res[1];
+    }
+}
+
+// Gradient of A_o + beta A_f.  Site n contributes Rm (x_{n,0} - y_n) e_0 and
+// -J_x f(x_n)^T w_n to x_n and w_n = beta Rf . eps_{n+1} to x_{n+1}; each gX
+// element receives exactly two FP64 atomic adds onto zero, whose result does
+// not depend on their order.  dA/dp = -sum_n J_p f(x_n)^T w_n (FP64 sums).
+template <class Model, class R>
+__global__ void __launch_bounds__(kBlock) grad_kernel(Ctx c, const double* Xe, const double* pe, double beta,
+                                                      double* gX, double* gp)
+{
+    constexpr int D = Model::D, NP = Model::NP;
+    __shared__ double wsum[NP][kBlock / 32];
+    __shared__ int last;
+    __shared__ double res[NP];
+    R pr[kMaxP];
+    Model::prep(pe ? pe : c.st->p, pr);
+    double vp[NP];
+    for (int l = 0; l < NP; ++l) vp[l] = 0.0;
+    const R* y = (const R*)c.y;
+    const int64_t ld = c.M + 1;
+    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n <= c.M; n += (int64_t)gridDim.x * kBlock) {
+        R x[D], gx[D];
+        for (int a = 0; a < D; ++a) { x[a] = path_at<R>(c, Xe, a, n); gx[a] = R(0); }
+        double own[D];
+        for (int a = 0; a < D; ++a) own[a] = 0.0;
+        if (n >= 1) own[0] = c.Rm * (double)(x[0] - y[n]);
+        if (n < c.M) {
+            R w[D], f[D], fx[D], gpl[kMaxP];
+            for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
+            // f(x_n) first, for the residual that seeds the cotangent
+            rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), fx);
+            for (int a = 0; a < D; ++a) w[a] = R(beta * c.Rf[a]) * (path_at<R>(c, Xe, a, n + 1) - fx[a]);
+            rk4_vjp<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), w, f, gx, gpl);
+            for (int a = 0; a < D; ++a) {
+                own[a] -= (double)gx[a];
+                atomicAdd(&gX[a * ld + n + 1], (double)w[a]);
+            }
+            for (int l = 0; l < NP; ++l) vp[l] -= (double)gpl[l];
+        }
+        for (int a = 0; a < D; ++a) atomicAdd(&gX[a * ld + n], own[a]);
+    }
+    grid_sums_last_block<NP>(c, vp, res, wsum, &last);
+    if (last && threadIdx.x == 0)
+        for (int l = 0; l < NP; ++l) gp[l] = res[l];
+}
+
+template <class R>
+__global__ void convert_kernel(const double* src, R* dst, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = R(src[i]);
+}
+
+// Handle storage <-> dense FP64 [D][M+1].
+template <class R>
+__global__ void path_io_kernel(Ctx c, int D, double* dense, int to_state)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)D * (c.M + 1);
+    if (i >= tot) return;
+    const int64_t a = i / (c.M + 1), n = i - a * (c.M + 1);
+    R* X = (R*)c.X;
+    if (to_state) X[a * c.ldx + n] = R(dense[i]);
+    else dense[i] = (double)X[a * c.ldx + n];
+}
+
+// ---------------------------------------------------------------------------
+
+template <class Model, class R> static cudaError_t init_t(const Ctx& c, cudaStream_t s)
+{
+    init_path_kernel<Model, R><<<(unsigned)((c.M + 1 + 255) / 256), 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+template <class Model, class R> static cudaError_t refresh_t(const Ctx& c, cudaStream_t s)
+{
+    refresh_cache_kernel<Model, R><<<(unsigned)((c.M + 255) / 256), 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+static int reduce_grid(int64_t M)
+{
+    int64_t g = (M + 1 + kBlock - 1) / kBlock;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return (int)(g < 1 ? 1 : g);
+}
+template <class Model, class R>
+static cudaError_t action_t(const Ctx& c, const double* Xe, const double* pe, double* out, cudaStream_t s)
+{
+    action_kernel<Model, R><<<reduce_grid(c.M), kBlock, 0, s>>>(c, Xe, pe, out);
+    return cudaGetLastError();
+}
+template <class Model, class R>
+static cudaError_t grad_t(const Ctx& c, const double* Xe, const double* pe, double beta, double* gX, double* gp,
+                          cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(gX, 0, sizeof(double) * (size_t)Model::D * (size_t)(c.M + 1), s);
+    if (e != cudaSuccess) return e;
+    grad_kernel<Model, R><<<reduce_grid(c.M), kBlock, 0, s>>>(c, Xe, pe, beta, gX, gp);
+    return cudaGetLastError();
+}
+
+#define PIMC_DISPATCH(FN, ...)                                                            \
+    do {                                                                                  \
+        if (prec == 0) {                                                                  \
+            if (model == 0) return FN<HH<double>, double>(__VA_ARGS__);                   \
+            if (model == 1) return FN<LinGauss<double>, double>(__VA_ARGS__);             \
+            return FN<Toy1D<double>, double>(__VA_ARGS__);                                \
+        }                                                                                 \
+        if (model == 0) return FN<HH<float>, float>(__VA_ARGS__);                         \
+        if (model == 1) return FN<LinGauss<float>, float>(__VA_ARGS__);                   \
+        return FN<Toy1D<float>, float>(__VA_ARGS__);                                      \
+    } while (0)
+
+cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s) { PIMC_DISPATCH(init_t, c, s); }
+cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s)
+{
+    PIMC_DISPATCH(refresh_t, c, s);
+}
+cudaError_t launch_action(int model, int prec, const Ctx& c, const double* X_ext, const double* p_ext, double* out,
+                          cudaStream_t s)
+{
+    PIMC_DISPATCH(action_t, c, X_ext, p_ext, out, s);
+}
+cudaError_t launch_grad(int model, int prec, const Ctx& c, const double* X_ext, const double* p_ext, double beta,
+                        double* gX, double* gp, cudaStream_t s)
+{
+    PIMC_DISPATCH(grad_t, c, X_ext, p_ext, beta, gX, gp, s);
+}
+cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid == 0) return cudaSuccess;
+    if (prec == 0) convert_kernel<double><<<grid, 256, 0, s>>>(src, (double*)dst, n);
+    else convert_kernel<float><<<grid, 256, 0, s>>>(src, (float*)dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_path_io(int prec, const Ctx& c, int D, double* dense, int to_state, cudaStream_t s)
+{
+    const int64_t tot = (int64_t)D * (c.M + 1);
+    const unsigned grid = (unsigned)((tot + 255) / 256);
+    if (prec == 0) path_io_kernel<double><<<grid, 256, 0, s>>>(c, D, dense, to_state);
+    else path_io_kernel<float><<<grid, 256, 0, s>>>(c, D, dense, to_state);
+    return cudaGetLastError();
+}
+
+}  // namespace pimc

@@ -1,0 +1,921 @@
+// Host runtime behind the C ABI of include/pimc.h: the handle, its device
+// buffers, argument validation, launch geometry, statistics read-back and
+// checkpoints.  All arithmetic of the sampler runs in the kernels of sweep.cu
+// and ops.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pimc.h"
+#include "internal.h"
+
+using namespace pimc;
+
+struct pimc_handle_s {
+    int model = 0, D = 0, NP = 0, prec = 0;
+    int64_t M = 0, ldx = 0, ldf = 0;
+    double dt = 0, Rm = 0, Rf[4] = {0, 0, 0, 0};
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device buffers (sized for FP64 elements; FP32 storage uses the first half)
+    void* X = nullptr;
+    void* F[2] = {nullptr, nullptr};
+    void* y = nullptr;
+    void* I = nullptr;
+    void* sig = nullptr;
+    uint32_t* acc_win = nullptr;
+    DevState* st = nullptr;
+    double* partials = nullptr;
+    unsigned* bar = nullptr;
+    unsigned* ticket = nullptr;
+    double* red = nullptr;
+    double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
+    unsigned long long* hist = nullptr;
+    int64_t* h_comp = nullptr;
+    double *h_lo = nullptr, *h_hi = nullptr;
+    int n_sel = 0, n_bins = 0;
+    double* dense = nullptr;  // D*(M+1) FP64 staging
+    double* small = nullptr;  // 16 doubles of results
+    double* y64 = nullptr;    // FP64 copies of the data as given (M+1, M)
+    double* I64 = nullptr;
+    bool have_data = false, have_params = false;
+    DevState hs{};
+    int64_t n_init = 0, n_skip = 1, n_cool = 0;
+    double beta0 = 1.0, fbeta = 1.0, f_acc = 0.4, alpha = 0.0;
+    uint32_t chain = 0;
+    int64_t wait_ns = 2000000000LL;
+    int skip_cta = -1, grid_override = 0;
+    int grid = 1;
+    int64_t tile = 1;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(pimc_t h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CK(h, call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? PIMC_ERR_OOM : PIMC_ERR_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                            \
+    } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+size_t esize(pimc_t h) { return h->prec == PIMC_FP64 ? sizeof(double) : sizeof(float); }
+
+Ctx make_ctx(pimc_t h)
+{
+    Ctx c{};
+    c.M = h->M; c.ldx = h->ldx; c.ldf = h->ldf;
+    c.dt = h->dt; c.Rm = h->Rm;
+    for (int a = 0; a < 4; ++a) c.Rf[a] = h->Rf[a];
+    c.X = h->X; c.F[0] = h->F[0]; c.F[1] = h->F[1]; c.y = h->y; c.I = h->I; c.sig = h->sig;
+    c.acc_win = h->acc_win; c.st = h->st; c.partials = h->partials; c.bar = h->bar;
+    c.ticket = h->ticket; c.red = h->red;
+    c.S1 = h->S1; c.S2 = h->S2; c.shift = h->shift;
+    c.hist = h->hist; c.h_comp = h->h_comp; c.h_lo = h->h_lo; c.h_hi = h->h_hi;
+    c.n_sel = h->n_sel; c.n_bins = h->n_bins;
+    c.n_init = h->n_init; c.n_skip = h->n_skip; c.n_cool = h->n_cool;
+    c.fbeta = h->fbeta; c.f_acc = h->f_acc; c.alpha = h->alpha;
+    c.chain = h->chain; c.wait_ns = h->wait_ns; c.skip_cta = h->skip_cta;
+    c.tile = h->tile;
+    return c;
+}
+
+int pull_state(pimc_t h)
+{
+    CK(h, cudaMemcpyAsync(&h->hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIMC_OK;
+}
+
+int push_state(pimc_t h)
+{
+    CK(h, cudaMemcpyAsync(h->st, &h->hs, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIMC_OK;
+}
+
+// y and I in the storage precision, converted on the device from the FP64
+// copies (enqueued on the handle's stream).
+int convert_data(pimc_t h)
+{
+    CK(h, launch_convert(h->prec, h->y64, h->y, h->M + 1, h->stream));
+    CK(h, launch_convert(h->prec, h->I64, h->I, h->M, h->stream));
+    return PIMC_OK;
+}
+
+// Host FP64 arrays -> FP64 device copies -> storage precision.  Asynchronous
+// when the host arrays are pinned.
+int upload_data(pimc_t h, const double* y, const double* I)
+{
+    CK(h, cudaMemcpyAsync(h->y64, y, sizeof(double) * (h->M + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->I64, I, sizeof(double) * h->M, cudaMemcpyHostToDevice, h->stream));
+    return convert_data(h);
+}
+
+// Dense FP64 [D][M+1] host array -> handle storage (X or sig rows).
+int put_rows(pimc_t h, void* dst, const double* src)
+{
+    const int64_t n1 = h->M + 1;
+    if (h->prec == PIMC_FP64) {
+        CK(h, cudaMemcpy2D(dst, sizeof(double) * h->ldx, src, sizeof(double) * n1, sizeof(double) * n1, h->D,
+                           cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> t((size_t)(h->D * n1));
+        for (size_t i = 0; i < t.size(); ++i) t[i] = (float)src[i];
+        CK(h, cudaMemcpy2D(dst, sizeof(float) * h->ldx, t.data(), sizeof(float) * n1, sizeof(float) * n1, h->D,
+                           cudaMemcpyHostToDevice));
+    }
+    return PIMC_OK;
+}
+
+int get_rows(pimc_t h, double* dst, const void* src, int64_t ld, int64_t ncol)
+{
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->prec == PIMC_FP64) {
+        CK(h, cudaMemcpy2D(dst, sizeof(double) * ncol, src, sizeof(double) * ld, sizeof(double) * ncol, h->D,
+                           cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> t((size_t)(h->D * ncol));
+        CK(h, cudaMemcpy2D(t.data(), sizeof(float) * ncol, src, sizeof(float) * ld, sizeof(float) * ncol, h->D,
+                           cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < t.size(); ++i) dst[i] = (double)t[i];
+    }
+    return PIMC_OK;
+}
+
+int refresh(pimc_t h)
+{
+    if (!h->have_data || !h->have_params) return PIMC_OK;
+    CK(h, launch_refresh_cache(h->model, h->prec, make_ctx(h), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIMC_OK;
+}
+
+void choose_grid(pimc_t h)
+{
+    const int64_t sites = h->M + 1;
+    int maxco = sweep_max_grid(h->model, h->prec, h->device);
+    if (maxco < 1) maxco = 1;
+    if (maxco > kMaxGrid) maxco = kMaxGrid;
+    int64_t g;
+    if (h->grid_override > 0) {
+        g = h->grid_override;
+    } else {
+        const int64_t by_sm = std::min<int64_t>(h->num_sms, (sites + 63) / 64);
+        const int64_t by_threads = (sites + 2 * kBlock - 1) / (2 * kBlock);
+        g = std::max<int64_t>(by_sm, by_threads);
+    }
+    if (g > maxco) g = maxco;
+    if (g < 1) g = 1;
+    h->tile = (sites + g - 1) / g;
+    h->grid = (int)((sites + h->tile - 1) / h->tile);
+}
+
+int check_finite(const double* v, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return 0;
+    return 1;
+}
+
+void free_all(pimc_t h)
+{
+    void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar,
+                    h->ticket, h->red, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
+                    h->dense, h->small, h->y64, h->I64};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+// clear statistics, counters and windows (sweep counter and beta follow the schedule)
+int reset_stats(pimc_t h)
+{
+    const int64_t nc = (int64_t)h->D * (h->M + 1) + h->NP;
+    CK(h, cudaMemset(h->S1, 0, sizeof(double) * nc));
+    CK(h, cudaMemset(h->S2, 0, sizeof(double) * nc));
+    CK(h, cudaMemset(h->shift, 0, sizeof(double) * nc));
+    CK(h, cudaMemset(h->acc_win, 0, sizeof(uint32_t) * h->ldx));
+    if (h->hist) CK(h, cudaMemset(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
+    return PIMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, const double* Rm, const double* Rf)
+{
+    if (!out) return fail(nullptr, PIMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int Dm, NP;
+    switch (model) {
+    case PIMC_MODEL_HH: Dm = 4; NP = 7; break;
+    case PIMC_MODEL_LINGAUSS: Dm = 2; NP = 1; break;
+    case PIMC_MODEL_TOY1D: Dm = 1; NP = 1; break;
+    default: return fail(nullptr, PIMC_ERR_ARG, "unknown model %d", model);
+    }
+    if (M < 1 || M > (int64_t)1 << 31) return fail(nullptr, PIMC_ERR_ARG, "M must be in [1, 2^31], got %lld", (long long)M);
+    if (D != Dm) return fail(nullptr, PIMC_ERR_ARG, "model %d has D = %d, got %d", model, Dm, D);
+    if (L != 1) return fail(nullptr, PIMC_ERR_ARG, "only L = 1 (h(x) = x_0) is supported, got %d", L);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, PIMC_ERR_ARG, "dt must be finite and > 0");
+    if (!Rm || !(*Rm > 0.0) || !std::isfinite(*Rm)) return fail(nullptr, PIMC_ERR_ARG, "Rm must be finite and > 0");
+    if (!Rf) return fail(nullptr, PIMC_ERR_ARG, "Rf is NULL");
+    for (int a = 0; a < D; ++a)
+        if (!(Rf[a] >= 0.0) || !std::isfinite(Rf[a])) return fail(nullptr, PIMC_ERR_ARG, "Rf[%d] must be finite and >= 0", a);
+
+    pimc_t h = new pimc_handle_s();
+    h->model = model; h->D = D; h->NP = NP; h->M = M; h->dt = dt; h->Rm = *Rm;
+    for (int a = 0; a < D; ++a) h->Rf[a] = Rf[a];
+    h->ldx = round_up(M + 1, 64);
+    h->ldf = round_up(M, 64);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        int r = fail(nullptr, PIMC_ERR_CUDA, "device setup: %s", cudaGetErrorString(e));
+        delete h;
+        return r;
+    }
+    h->own_stream = true;
+    const int64_t nc = (int64_t)D * (M + 1) + NP;
+    struct { void** p; size_t bytes; } allocs[] = {
+        {&h->X, sizeof(double) * D * h->ldx},
+        {&h->F[0], sizeof(double) * D * h->ldf},
+        {&h->F[1], sizeof(double) * D * h->ldf},
+        {&h->y, sizeof(double) * h->ldx},
+        {&h->I, sizeof(double) * h->ldf},
+        {&h->sig, sizeof(double) * D * h->ldx},
+        {(void**)&h->acc_win, sizeof(uint32_t) * h->ldx},
+        {(void**)&h->st, sizeof(DevState)},
+        {(void**)&h->partials, sizeof(double) * 2 * kMaxGrid},
+        {(void**)&h->bar, sizeof(unsigned) * 4},
+        {(void**)&h->ticket, sizeof(unsigned) * 4},
+        {(void**)&h->red, sizeof(double) * 8 * kMaxGrid},
+        {(void**)&h->S1, sizeof(double) * nc},
+        {(void**)&h->S2, sizeof(double) * nc},
+        {(void**)&h->shift, sizeof(double) * nc},
+        {(void**)&h->dense, sizeof(double) * D * (M + 1)},
+        {(void**)&h->small, sizeof(double) * 16},
+        {(void**)&h->y64, sizeof(double) * (M + 1)},
+        {(void**)&h->I64, sizeof(double) * M},
+    };
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            int r = fail(nullptr, e == cudaErrorMemoryAllocation ? PIMC_ERR_OOM : PIMC_ERR_CUDA,
+                         "cudaMalloc(%zu): %s", a.bytes, cudaGetErrorString(e));
+            free_all(h);
+            cudaStreamDestroy(h->stream);
+            delete h;
+            return r;
+        }
+    }
+    cudaMemset(h->bar, 0, sizeof(unsigned) * 4);
+    cudaMemset(h->ticket, 0, sizeof(unsigned) * 4);
+    cudaMemset(h->X, 0, sizeof(double) * D * h->ldx);
+    cudaMemset(h->F[0], 0, sizeof(double) * D * h->ldf);
+    cudaMemset(h->F[1], 0, sizeof(double) * D * h->ldf);
+    cudaMemset(h->sig, 0, sizeof(double) * D * h->ldx);
+    h->hs = DevState{};
+    h->hs.beta = 1.0;
+    for (int l = 0; l < kMaxParams; ++l) { h->hs.lo[l] = -INFINITY; h->hs.hi[l] = INFINITY; }
+    cudaMemset(h->y64, 0, sizeof(double) * (M + 1));
+    cudaMemset(h->I64, 0, sizeof(double) * M);
+    int r = push_state(h);
+    if (r == PIMC_OK) r = reset_stats(h);
+    if (r != PIMC_OK) {
+        g_create_error = h->err;
+        pimc_destroy(h);
+        return r;
+    }
+    choose_grid(h);
+    *out = h;
+    return PIMC_OK;
+}
+
+int pimc_destroy(pimc_t h)
+{
+    if (!h) return PIMC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return PIMC_OK;
+}
+
+const char* pimc_last_error(pimc_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int pimc_set_stream(pimc_t h, void* stream)
+{
+    if (!h) return PIMC_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    h->own_stream = false;
+    h->stream = (cudaStream_t)stream;
+    return PIMC_OK;
+}
+
+int pimc_set_precision(pimc_t h, int precision)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (precision != PIMC_FP64 && precision != PIMC_FP32_MIXED)
+        return fail(h, PIMC_ERR_ARG, "unknown precision %d", precision);
+    if (precision == h->prec) return PIMC_OK;
+    const int64_t nd = (int64_t)h->D * (h->M + 1);
+    std::vector<double> X(nd), S(nd);
+    int r = get_rows(h, X.data(), h->X, h->ldx, h->M + 1);
+    if (r == PIMC_OK) r = get_rows(h, S.data(), h->sig, h->ldx, h->M + 1);
+    if (r != PIMC_OK) return r;
+    h->prec = precision;
+    if ((r = put_rows(h, h->X, X.data())) != PIMC_OK) return r;
+    if ((r = put_rows(h, h->sig, S.data())) != PIMC_OK) return r;
+    if (h->have_data && (r = convert_data(h)) != PIMC_OK) return r;
+    choose_grid(h);
+    return refresh(h);
+}
+
+int pimc_set_data(pimc_t h, const double* y, const double* I_inj)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!y || !I_inj) return fail(h, PIMC_ERR_ARG, "y or I_inj is NULL");
+    if (!check_finite(y, h->M + 1)) return fail(h, PIMC_ERR_ARG, "y has non-finite values");
+    if (!check_finite(I_inj, h->M)) return fail(h, PIMC_ERR_ARG, "I_inj has non-finite values");
+    int r = upload_data(h, y, I_inj);
+    if (r != PIMC_OK) return r;
+    h->have_data = true;
+    CK(h, launch_init_path(h->model, h->prec, make_ctx(h), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return refresh(h);
+}
+
+int pimc_load_data(pimc_t h, const double* y, const double* I_inj)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data) return fail(h, PIMC_ERR_STATE, "pimc_load_data before pimc_set_data");
+    if (!y || !I_inj) return fail(h, PIMC_ERR_ARG, "y or I_inj is NULL");
+    if (!check_finite(y, h->M + 1)) return fail(h, PIMC_ERR_ARG, "y has non-finite values");
+    if (!check_finite(I_inj, h->M)) return fail(h, PIMC_ERR_ARG, "I_inj has non-finite values");
+    int r = upload_data(h, y, I_inj);
+    if (r != PIMC_OK) return r;
+    if (h->have_params) CK(h, launch_refresh_cache(h->model, h->prec, make_ctx(h), h->stream));
+    return PIMC_OK;
+}
+
+int pimc_set_params(pimc_t h, const double* p, const double* lo, const double* hi, const uint8_t* free_mask, int Np)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (Np != h->NP) return fail(h, PIMC_ERR_ARG, "model has Np = %d, got %d", h->NP, Np);
+    if (!p) return fail(h, PIMC_ERR_ARG, "p is NULL");
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    unsigned mask = 0;
+    for (int l = 0; l < Np; ++l) {
+        const double L = lo ? lo[l] : -INFINITY, H = hi ? hi[l] : INFINITY;
+        const int fr = free_mask ? (free_mask[l] != 0) : 0;
+        if (!std::isfinite(p[l])) return fail(h, PIMC_ERR_ARG, "p[%d] is not finite", l);
+        if (std::isnan(L) || std::isnan(H) || L > H) return fail(h, PIMC_ERR_ARG, "bad bounds for p[%d]", l);
+        if (fr && !(p[l] >= L && p[l] <= H)) return fail(h, PIMC_ERR_ARG, "p[%d] outside its prior box", l);
+        h->hs.p[l] = p[l]; h->hs.lo[l] = L; h->hs.hi[l] = H;
+        if (fr) mask |= 1u << l;
+    }
+    h->hs.free_mask = mask;
+    if ((r = push_state(h)) != PIMC_OK) return r;
+    h->have_params = true;
+    return refresh(h);
+}
+
+int pimc_set_path(pimc_t h, const double* X)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!X) {
+        if (!h->have_data) return fail(h, PIMC_ERR_STATE, "default path needs pimc_set_data first");
+        CK(h, launch_init_path(h->model, h->prec, make_ctx(h), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return refresh(h);
+    }
+    if (!check_finite(X, (int64_t)h->D * (h->M + 1))) return fail(h, PIMC_ERR_ARG, "X has non-finite values");
+    int r = put_rows(h, h->X, X);
+    if (r != PIMC_OK) return r;
+    return refresh(h);
+}
+
+int pimc_set_steps(pimc_t h, const double* sigma_x, int per_site, const double* sigma_p)
+{
+    if (!h) return PIMC_ERR_ARG;
+    const int64_t n1 = h->M + 1, nd = (int64_t)h->D * n1;
+    if (sigma_x) {
+        std::vector<double> S(nd);
+        for (int a = 0; a < h->D; ++a)
+            for (int64_t n = 0; n < n1; ++n) S[a * n1 + n] = per_site ? sigma_x[a * n1 + n] : sigma_x[a];
+        for (double v : S)
+            if (!(v >= 0.0) || !std::isfinite(v)) return fail(h, PIMC_ERR_ARG, "sigma_x must be finite and >= 0");
+        int r = put_rows(h, h->sig, S.data());
+        if (r != PIMC_OK) return r;
+    }
+    if (sigma_p) {
+        int r = pull_state(h);
+        if (r != PIMC_OK) return r;
+        for (int l = 0; l < h->NP; ++l) {
+            if (!(sigma_p[l] >= 0.0) || !std::isfinite(sigma_p[l])) return fail(h, PIMC_ERR_ARG, "sigma_p must be finite and >= 0");
+            h->hs.sigp[l] = sigma_p[l];
+        }
+        return push_state(h);
+    }
+    return PIMC_OK;
+}
+
+int pimc_set_schedule(pimc_t h, int64_t n_init, int64_t n_skip, double beta0, int64_t n_cool, double f_acc, double alpha)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (n_skip < 1 || n_init < 0 || n_cool < 0 || !(beta0 > 0.0) || beta0 > 1.0 || !std::isfinite(f_acc) ||
+        !std::isfinite(alpha))
+        return fail(h, PIMC_ERR_ARG, "bad schedule");
+    h->n_init = n_init; h->n_skip = n_skip; h->n_cool = n_cool; h->beta0 = beta0;
+    h->f_acc = f_acc; h->alpha = alpha;
+    h->fbeta = n_cool > 0 ? std::pow(1.0 / beta0, 1.0 / (double)n_cool) : 1.0;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    h->hs.sweep = 0;
+    h->hs.J = 0;
+    h->hs.beta = n_cool > 0 ? beta0 : 1.0;
+    for (int l = 0; l < kMaxParams; ++l) { h->hs.accp_win[l] = 0; h->hs.par_acc[l] = 0; h->hs.par_prop[l] = 0; }
+    h->hs.site_acc[0] = h->hs.site_acc[1] = h->hs.site_prop[0] = h->hs.site_prop[1] = h->hs.nonfinite = 0;
+    if ((r = push_state(h)) != PIMC_OK) return r;
+    return reset_stats(h);
+}
+
+int pimc_set_chain(pimc_t h, uint32_t chain)
+{
+    if (!h) return PIMC_ERR_ARG;
+    h->chain = chain;
+    return PIMC_OK;
+}
+
+int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_sweep before pimc_set_data/pimc_set_params");
+    if (n_sweeps < 0) return fail(h, PIMC_ERR_ARG, "n_sweeps < 0");
+    Ctx c = make_ctx(h);
+    c.seed = seed;
+    const int64_t chunk = 4096;  // bound the duration of one launch
+    for (int64_t done = 0; done < n_sweeps; done += chunk) {
+        const int64_t k = std::min<int64_t>(chunk, n_sweeps - done);
+        CK(h, launch_sweep(h->model, h->prec, c, k, h->grid, h->stream));
+    }
+    return PIMC_OK;
+}
+
+int pimc_sync(pimc_t h)
+{
+    if (!h) return PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    if (h->hs.status & kStatusTimeout) {
+        h->hs.status = 0;
+        h->hs.abort = 0;
+        CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->stream));
+        if ((r = push_state(h)) != PIMC_OK) return r;
+        return fail(h, PIMC_ERR_TIMEOUT, "a bounded grid-barrier wait expired; the sweep launch returned early");
+    }
+    return PIMC_OK;
+}
+
+int pimc_action(pimc_t h, double* A_out, double* Ao_out, double* Af_out)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_action before data/params");
+    CK(h, launch_action(h->model, h->prec, make_ctx(h), nullptr, nullptr, h->small, h->stream));
+    double r[3];
+    CK(h, cudaMemcpyAsync(r, h->small, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (A_out) *A_out = r[0];
+    if (Ao_out) *Ao_out = r[1];
+    if (Af_out) *Af_out = r[2];
+    return PIMC_OK;
+}
+
+int pimc_grad(pimc_t h, double beta, double* gX, double* gp)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_grad before data/params");
+    if (!gX || !gp) return fail(h, PIMC_ERR_ARG, "NULL output");
+    CK(h, launch_grad(h->model, h->prec, make_ctx(h), nullptr, nullptr, beta, h->dense, h->small, h->stream));
+    CK(h, cudaMemcpyAsync(gX, h->dense, sizeof(double) * h->D * (h->M + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(gp, h->small, sizeof(double) * h->NP, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIMC_OK;
+}
+
+int pimc_action_dev(pimc_t h, const double* X_dev, const double* p_dev, double* out_dev, void* stream)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data) return fail(h, PIMC_ERR_STATE, "pimc_action_dev before pimc_set_data");
+    if (!X_dev || !p_dev || !out_dev) return fail(h, PIMC_ERR_ARG, "NULL device pointer");
+    CK(h, launch_action(h->model, h->prec, make_ctx(h), X_dev, p_dev, out_dev, (cudaStream_t)stream));
+    return PIMC_OK;
+}
+
+int pimc_grad_dev(pimc_t h, const double* X_dev, const double* p_dev, double beta, double* gX_dev, double* gp_dev,
+                  void* stream)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data) return fail(h, PIMC_ERR_STATE, "pimc_grad_dev before pimc_set_data");
+    if (!X_dev || !p_dev || !gX_dev || !gp_dev) return fail(h, PIMC_ERR_ARG, "NULL device pointer");
+    CK(h, launch_grad(h->model, h->prec, make_ctx(h), X_dev, p_dev, beta, gX_dev, gp_dev, (cudaStream_t)stream));
+    return PIMC_OK;
+}
+
+int pimc_site_delta(pimc_t h, const double* Xp, double beta, double* dA_out)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_site_delta before data/params");
+    if (!Xp || !dA_out) return fail(h, PIMC_ERR_ARG, "NULL argument");
+    const int64_t nd = (int64_t)h->D * (h->M + 1);
+    double* dA = nullptr;
+    CK(h, cudaMalloc(&dA, sizeof(double) * (h->M + 1)));
+    cudaError_t e = cudaMemcpyAsync(h->dense, Xp, sizeof(double) * nd, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_site_delta(h->model, h->prec, make_ctx(h), h->dense, beta, dA, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dA_out, dA, sizeof(double) * (h->M + 1), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dA);
+    CK(h, e);
+    return PIMC_OK;
+}
+
+int pimc_param_delta(pimc_t h, int l, double pl_new, double beta, double* dA_out)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_param_delta before data/params");
+    if (l < 0 || l >= h->NP || !dA_out) return fail(h, PIMC_ERR_ARG, "bad parameter index or NULL output");
+    CK(h, launch_param_delta(h->model, h->prec, make_ctx(h), l, pl_new, beta, h->small, h->stream));
+    CK(h, cudaMemcpyAsync(dA_out, h->small, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PIMC_OK;
+}
+
+int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples)
+{
+    if (!h) return PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    const int64_t nc = (int64_t)h->D * (h->M + 1) + h->NP;
+    std::vector<double> S1(nc), S2(nc), sh(nc);
+    CK(h, cudaMemcpy(S1.data(), h->S1, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(S2.data(), h->S2, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(sh.data(), h->shift, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    const double J = (double)h->hs.J;
+    for (int64_t c = 0; c < nc; ++c) {
+        if (mean) mean[c] = h->hs.J > 0 ? sh[c] + S1[c] / J : NAN;
+        if (var) var[c] = h->hs.J > 1 ? (S2[c] - S1[c] * S1[c] / J) / (J - 1.0) : NAN;
+    }
+    if (n_samples) *n_samples = h->hs.J;
+    return PIMC_OK;
+}
+
+int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const double* lo, const double* hi, int n_bins)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (n_sel < 1 || n_sel > kMaxSel || n_bins < 1 || n_bins > kMaxBins || !comp_index || !lo || !hi)
+        return fail(h, PIMC_ERR_ARG, "bad histogram configuration");
+    const int64_t nc = (int64_t)h->D * (h->M + 1) + h->NP;
+    for (int k = 0; k < n_sel; ++k) {
+        if (comp_index[k] < 0 || comp_index[k] >= nc) return fail(h, PIMC_ERR_ARG, "component index out of range");
+        if (!(lo[k] < hi[k]) || !std::isfinite(lo[k]) || !std::isfinite(hi[k]))
+            return fail(h, PIMC_ERR_ARG, "histogram range must be finite with lo < hi");
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->hist) {
+        CK(h, cudaMalloc(&h->hist, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
+        CK(h, cudaMalloc(&h->h_comp, sizeof(int64_t) * kMaxSel));
+        CK(h, cudaMalloc(&h->h_lo, sizeof(double) * kMaxSel));
+        CK(h, cudaMalloc(&h->h_hi, sizeof(double) * kMaxSel));
+    }
+    CK(h, cudaMemset(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
+    CK(h, cudaMemcpy(h->h_comp, comp_index, sizeof(int64_t) * n_sel, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->h_lo, lo, sizeof(double) * n_sel, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->h_hi, hi, sizeof(double) * n_sel, cudaMemcpyHostToDevice));
+    h->n_sel = n_sel;
+    h->n_bins = n_bins;
+    return PIMC_OK;
+}
+
+int pimc_histograms(pimc_t h, uint64_t* counts)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->hist || h->n_sel == 0) return fail(h, PIMC_ERR_STATE, "no histograms configured");
+    if (!counts) return fail(h, PIMC_ERR_ARG, "counts is NULL");
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(counts, h->hist, sizeof(uint64_t) * h->n_sel * (h->n_bins + 2), cudaMemcpyDeviceToHost));
+    return PIMC_OK;
+}
+
+int pimc_histogram_shape(pimc_t h, int* n_sel, int* n_bins)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (n_sel) *n_sel = h->n_sel;
+    if (n_bins) *n_bins = h->n_bins;
+    return PIMC_OK;
+}
+
+int pimc_get_state(pimc_t h, double* X, double* p)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (X) {
+        int r = get_rows(h, X, h->X, h->ldx, h->M + 1);
+        if (r != PIMC_OK) return r;
+    }
+    if (p) {
+        int r = pull_state(h);
+        if (r != PIMC_OK) return r;
+        for (int l = 0; l < h->NP; ++l) p[l] = h->hs.p[l];
+    }
+    return PIMC_OK;
+}
+
+int pimc_get_steps(pimc_t h, double* sigma_x, double* sigma_p)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (sigma_x) {
+        int r = get_rows(h, sigma_x, h->sig, h->ldx, h->M + 1);
+        if (r != PIMC_OK) return r;
+    }
+    if (sigma_p) {
+        int r = pull_state(h);
+        if (r != PIMC_OK) return r;
+        for (int l = 0; l < h->NP; ++l) sigma_p[l] = h->hs.sigp[l];
+    }
+    return PIMC_OK;
+}
+
+int pimc_get_sweep(pimc_t h, int64_t* sweep, double* beta)
+{
+    if (!h) return PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    if (sweep) *sweep = h->hs.sweep;
+    if (beta) *beta = h->hs.beta;
+    return PIMC_OK;
+}
+
+int pimc_accept_stats(pimc_t h, uint64_t* site_acc, uint64_t* site_prop, uint64_t* par_acc, uint64_t* par_prop)
+{
+    if (!h) return PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    for (int k = 0; k < 2; ++k) {
+        if (site_acc) site_acc[k] = h->hs.site_acc[k];
+        if (site_prop) site_prop[k] = h->hs.site_prop[k];
+    }
+    for (int l = 0; l < h->NP; ++l) {
+        if (par_acc) par_acc[l] = h->hs.par_acc[l];
+        if (par_prop) par_prop[l] = h->hs.par_prop[l];
+    }
+    return PIMC_OK;
+}
+
+int pimc_launch_info(pimc_t h, int* grid, int* block)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (grid) *grid = h->grid;
+    if (block) *block = kBlock;
+    return PIMC_OK;
+}
+
+int pimc_set_wait_limit(pimc_t h, int64_t ns)
+{
+    if (!h || ns < 1000) return h ? fail(h, PIMC_ERR_ARG, "wait limit must be >= 1000 ns") : PIMC_ERR_ARG;
+    h->wait_ns = ns;
+    return PIMC_OK;
+}
+
+int pimc_debug_skip_arrive(pimc_t h, int cta)
+{
+    if (!h) return PIMC_ERR_ARG;
+    h->skip_cta = cta;
+    return PIMC_OK;
+}
+
+int pimc_set_grid(pimc_t h, int grid)
+{
+    if (!h || grid < 0) return h ? fail(h, PIMC_ERR_ARG, "grid must be >= 0") : PIMC_ERR_ARG;
+    h->grid_override = grid;
+    choose_grid(h);
+    return PIMC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints: "PIMCCKPT" magic, version, then a payload of fixed-size
+// sections, then a CRC-32 (IEEE 802.3 polynomial, reflected) of the payload.
+// ---------------------------------------------------------------------------
+namespace {
+
+uint32_t crc32(const unsigned char* d, size_t n)
+{
+    uint32_t c = 0xFFFFFFFFu;
+    for (size_t i = 0; i < n; ++i) {
+        c ^= d[i];
+        for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    }
+    return ~c;
+}
+
+struct Writer {
+    std::vector<unsigned char> b;
+    void put(const void* p, size_t n) { b.insert(b.end(), (const unsigned char*)p, (const unsigned char*)p + n); }
+    template <class T> void val(const T& v) { put(&v, sizeof v); }
+};
+
+struct Reader {
+    const unsigned char* p;
+    size_t n, off = 0;
+    bool get(void* d, size_t k)
+    {
+        if (off + k > n) return false;
+        memcpy(d, p + off, k);
+        off += k;
+        return true;
+    }
+    template <class T> bool val(T& v) { return get(&v, sizeof v); }
+};
+
+const char kMagic[8] = {'P', 'I', 'M', 'C', 'C', 'K', 'P', 'T'};
+const uint32_t kVersion = 1;
+
+}  // namespace
+
+extern "C" int pimc_checkpoint_save(pimc_t h, const char* path)
+{
+    if (!h || !path) return h ? fail(h, PIMC_ERR_ARG, "path is NULL") : PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    const int64_t n1 = h->M + 1, nd = (int64_t)h->D * n1, nc = nd + h->NP;
+    std::vector<double> X(nd), S(nd), F0((size_t)(h->D * h->M)), F1((size_t)(h->D * h->M)), S1(nc), S2(nc), SH(nc);
+    if ((r = get_rows(h, X.data(), h->X, h->ldx, n1)) != PIMC_OK) return r;
+    if ((r = get_rows(h, S.data(), h->sig, h->ldx, n1)) != PIMC_OK) return r;
+    if ((r = get_rows(h, F0.data(), h->F[0], h->ldf, h->M)) != PIMC_OK) return r;
+    if ((r = get_rows(h, F1.data(), h->F[1], h->ldf, h->M)) != PIMC_OK) return r;
+    std::vector<uint32_t> acc((size_t)n1);
+    CK(h, cudaMemcpy(acc.data(), h->acc_win, sizeof(uint32_t) * n1, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(S1.data(), h->S1, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(S2.data(), h->S2, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(SH.data(), h->shift, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> hist;
+    std::vector<int64_t> hc(h->n_sel);
+    std::vector<double> hl(h->n_sel), hh(h->n_sel);
+    if (h->n_sel > 0) {
+        hist.resize((size_t)h->n_sel * (h->n_bins + 2));
+        CK(h, cudaMemcpy(hist.data(), h->hist, sizeof(unsigned long long) * hist.size(), cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(hc.data(), h->h_comp, sizeof(int64_t) * h->n_sel, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(hl.data(), h->h_lo, sizeof(double) * h->n_sel, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(hh.data(), h->h_hi, sizeof(double) * h->n_sel, cudaMemcpyDeviceToHost));
+    }
+    Writer w;
+    w.val(h->model); w.val(h->prec); w.val(h->M); w.val(h->D); w.val(h->NP);
+    w.val(h->dt); w.val(h->Rm); w.put(h->Rf, sizeof h->Rf);
+    w.val(h->n_init); w.val(h->n_skip); w.val(h->n_cool);
+    w.val(h->beta0); w.val(h->fbeta); w.val(h->f_acc); w.val(h->alpha); w.val(h->chain);
+    w.val(h->hs);
+    std::vector<double> yh(n1), Ih(h->M);
+    CK(h, cudaMemcpy(yh.data(), h->y64, sizeof(double) * n1, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(Ih.data(), h->I64, sizeof(double) * h->M, cudaMemcpyDeviceToHost));
+    w.put(yh.data(), sizeof(double) * n1);
+    w.put(Ih.data(), sizeof(double) * h->M);
+    w.put(X.data(), sizeof(double) * nd);
+    w.put(S.data(), sizeof(double) * nd);
+    w.put(F0.data(), sizeof(double) * F0.size());
+    w.put(F1.data(), sizeof(double) * F1.size());
+    w.put(acc.data(), sizeof(uint32_t) * n1);
+    w.put(S1.data(), sizeof(double) * nc);
+    w.put(S2.data(), sizeof(double) * nc);
+    w.put(SH.data(), sizeof(double) * nc);
+    w.val(h->n_sel); w.val(h->n_bins);
+    if (h->n_sel > 0) {
+        w.put(hc.data(), sizeof(int64_t) * hc.size());
+        w.put(hl.data(), sizeof(double) * hl.size());
+        w.put(hh.data(), sizeof(double) * hh.size());
+        w.put(hist.data(), sizeof(unsigned long long) * hist.size());
+    }
+    const uint32_t crc = crc32(w.b.data(), w.b.size());
+    const uint64_t len = w.b.size();
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(h, PIMC_ERR_IO, "cannot open %s for writing", path);
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&kVersion, 4, 1, f) == 1 && fwrite(&len, 8, 1, f) == 1 &&
+              fwrite(w.b.data(), 1, w.b.size(), f) == w.b.size() && fwrite(&crc, 4, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? PIMC_OK : fail(h, PIMC_ERR_IO, "short write to %s", path);
+}
+
+extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
+{
+    if (!h || !path) return h ? fail(h, PIMC_ERR_ARG, "path is NULL") : PIMC_ERR_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(h, PIMC_ERR_IO, "cannot open %s", path);
+    char magic[8];
+    uint32_t ver = 0, crc = 0;
+    uint64_t len = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(&ver, 4, 1, f) == 1 &&
+              ver == kVersion && fread(&len, 8, 1, f) == 1 && len < ((uint64_t)1 << 40);
+    std::vector<unsigned char> buf;
+    if (ok) {
+        buf.resize((size_t)len);
+        ok = fread(buf.data(), 1, buf.size(), f) == buf.size() && fread(&crc, 4, 1, f) == 1;
+    }
+    fclose(f);
+    if (!ok) return fail(h, PIMC_ERR_IO, "%s: not a checkpoint of this version, or truncated", path);
+    if (crc32(buf.data(), buf.size()) != crc) return fail(h, PIMC_ERR_IO, "%s: CRC mismatch", path);
+    Reader rd{buf.data(), buf.size()};
+    int model, prec, D, NP;
+    int64_t M;
+    double dt, Rm, Rf[4];
+    ok = rd.val(model) && rd.val(prec) && rd.val(M) && rd.val(D) && rd.val(NP) && rd.val(dt) && rd.val(Rm) &&
+         rd.get(Rf, sizeof Rf);
+    if (!ok || model != h->model || M != h->M || D != h->D || NP != h->NP)
+        return fail(h, PIMC_ERR_IO, "%s: checkpoint of a different problem shape", path);
+    h->dt = dt; h->Rm = Rm;
+    memcpy(h->Rf, Rf, sizeof Rf);
+    DevState hs{};
+    ok = rd.val(h->n_init) && rd.val(h->n_skip) && rd.val(h->n_cool) && rd.val(h->beta0) && rd.val(h->fbeta) &&
+         rd.val(h->f_acc) && rd.val(h->alpha) && rd.val(h->chain) && rd.val(hs);
+    const int64_t n1 = M + 1, nd = (int64_t)D * n1, nc = nd + NP;
+    std::vector<double> y(n1), I(M), X(nd), S(nd), F0((size_t)(D * M)), F1((size_t)(D * M)), S1(nc), S2(nc), SH(nc);
+    std::vector<uint32_t> acc(n1);
+    ok = ok && rd.get(y.data(), sizeof(double) * n1) && rd.get(I.data(), sizeof(double) * M) &&
+         rd.get(X.data(), sizeof(double) * nd) && rd.get(S.data(), sizeof(double) * nd) &&
+         rd.get(F0.data(), sizeof(double) * F0.size()) && rd.get(F1.data(), sizeof(double) * F1.size()) &&
+         rd.get(acc.data(), sizeof(uint32_t) * n1) && rd.get(S1.data(), sizeof(double) * nc) &&
+         rd.get(S2.data(), sizeof(double) * nc) && rd.get(SH.data(), sizeof(double) * nc);
+    int n_sel = 0, n_bins = 0;
+    ok = ok && rd.val(n_sel) && rd.val(n_bins);
+    if (!ok) return fail(h, PIMC_ERR_IO, "%s: truncated payload", path);
+    std::vector<int64_t> hc(n_sel > 0 ? n_sel : 0);
+    std::vector<double> hl(hc.size()), hh(hc.size());
+    std::vector<unsigned long long> hist;
+    if (n_sel > 0) {
+        hist.resize((size_t)n_sel * (n_bins + 2));
+        ok = rd.get(hc.data(), sizeof(int64_t) * n_sel) && rd.get(hl.data(), sizeof(double) * n_sel) &&
+             rd.get(hh.data(), sizeof(double) * n_sel) &&
+             rd.get(hist.data(), sizeof(unsigned long long) * hist.size());
+        if (!ok) return fail(h, PIMC_ERR_IO, "%s: truncated histogram section", path);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->prec = prec;
+    int r = upload_data(h, y.data(), I.data());
+    if (r != PIMC_OK) return r;
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->have_data = true;
+    h->have_params = true;
+    if ((r = put_rows(h, h->X, X.data())) != PIMC_OK) return r;
+    if ((r = put_rows(h, h->sig, S.data())) != PIMC_OK) return r;
+    // cache rows are [D][M] with stride ldf
+    {
+        const size_t es = esize(h);
+        std::vector<unsigned char> t((size_t)D * M * es);
+        for (int b = 0; b < 2; ++b) {
+            const std::vector<double>& src = b == 0 ? F0 : F1;
+            for (size_t i = 0; i < src.size(); ++i) {
+                if (prec == PIMC_FP64) memcpy(&t[i * es], &src[i], es);
+                else { float v = (float)src[i]; memcpy(&t[i * es], &v, es); }
+            }
+            CK(h, cudaMemcpy2D(h->F[b], es * h->ldf, t.data(), es * M, es * M, D, cudaMemcpyHostToDevice));
+        }
+    }
+    CK(h, cudaMemcpy(h->acc_win, acc.data(), sizeof(uint32_t) * n1, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->S1, S1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->S2, S2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->shift, SH.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+    if (n_sel > 0) {
+        if ((r = pimc_set_histograms(h, n_sel, hc.data(), hl.data(), hh.data(), n_bins)) != PIMC_OK) return r;
+        CK(h, cudaMemcpy(h->hist, hist.data(), sizeof(unsigned long long) * hist.size(), cudaMemcpyHostToDevice));
+    }
+    hs.status = 0;
+    hs.abort = 0;
+    h->hs = hs;
+    CK(h, cudaMemset(h->bar, 0, sizeof(unsigned) * 4));
+    choose_grid(h);
+    return push_state(h);
+}

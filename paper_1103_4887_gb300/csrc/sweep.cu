@@ -1,0 +1,539 @@
+// The hot path: one persistent cooperative kernel runs whole checkerboard
+// sweeps (Fig. 1, Sec. 4.1).  Each CTA owns a contiguous tile of time steps.
+// Per sweep: even sites, grid barrier, odd sites, grid barrier, then each free
+// parameter in order -- every CTA computes the RK4 map at the proposed p for
+// its sites into the inactive half of the double-buffered f cache (Sec. 4.3)
+// and a partial change of action; after one grid barrier every CTA sums all
+// partials in the same fixed order (FP64) and takes the same accept decision,
+// so no second launch or broadcast is needed.  Statistics, step adaptation and
+// annealing follow in the same launch.  Barrier waits are bounded in time.
+#include <cuda/atomic>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace pimc {
+
+struct SweepShared {
+    double p[kMaxP], lo[kMaxP], hi[kMaxP], sigp[kMaxP];
+    double beta;
+    long long sweep, J;
+    unsigned fidx, free_mask, nred;
+    unsigned accp_win[kMaxP];
+    unsigned long long par_acc[kMaxP], par_prop[kMaxP];
+    double pnew, uacc;
+    double pq[kMaxP];
+    int inbox, abort;
+    double wsum[kBlock / 32];
+    unsigned long long site_acc[2], site_prop[2], nonfinite;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (generation counter).  The wait is bounded by c.wait_ns;
+// on expiry the CTA flags kStatusTimeout and the abort word, and every CTA
+// leaves the launch at its next barrier.  Returns false when leaving.
+__device__ bool grid_barrier(const Ctx& c, int* s_abort)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(c.bar[0]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(c.bar[1]);
+        cuda::atomic_ref<int, cuda::thread_scope_device> abrt(c.st->abort);
+        int ok = 1;
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        __threadfence();
+        if ((int)blockIdx.x != c.skip_cta) {
+            const unsigned prev = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+            if (prev == gridDim.x - 1) {
+                cnt.store(0u, cuda::memory_order_relaxed);
+                gen.store(g + 1u, cuda::memory_order_release);
+            }
+        }
+        if (gen.load(cuda::memory_order_acquire) == g) {
+            const unsigned long long t0 = global_ns();
+            unsigned ns = 32;
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (abrt.load(cuda::memory_order_relaxed)) { ok = 0; break; }
+                if ((long long)(global_ns() - t0) > c.wait_ns) {
+                    atomicOr(&c.st->status, kStatusTimeout);
+                    abrt.store(1, cuda::memory_order_relaxed);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 512) ns <<= 1;
+            }
+        }
+        __threadfence();
+        *s_abort = !ok;
+    }
+    __syncthreads();
+    return !*s_abort;
+}
+
+// Local change of action for x_n -> xp (Fig. 1 steps (c)-(g)): the
+// measurement term at n (n >= 1), the model-error term eps_n against the
+// cached f(x_{n-1}) (n >= 1) and eps_{n+1} against f(xp) (n <= M-1).
+template <class Model, class R>
+__device__ __forceinline__ R site_delta(const Ctx& c, int64_t n, const R* x, const R* xp, const R* fp,
+                                        R beta, const R* Fc)
+{
+    constexpr int D = Model::D;
+    const R* X = (const R*)c.X;
+    const R* y = (const R*)c.y;
+    R dA = R(0);
+    if (n >= 1) {
+        const R yn = y[n];
+        dA += sqdiff<R>(R(c.Rm), xp[0] - yn, x[0] - yn);
+        R dAf = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R fprev = Fc[a * c.ldf + n - 1];
+            dAf += sqdiff<R>(R(c.Rf[a]), xp[a] - fprev, x[a] - fprev);
+        }
+        dA += beta * dAf;
+    }
+    if (n < c.M) {
+        R dAf = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R xn1 = X[a * c.ldx + n + 1];
+            const R fc = Fc[a * c.ldf + n];
+            dAf += sqdiff<R>(R(c.Rf[a]), xn1 - fp[a], xn1 - fc);
+        }
+        dA += beta * dAf;
+    }
+    return dA;
+}
+
+// Proposal normals of site n at sweep s: D Box-Muller normals (cos then sin
+// per pair of blocks 0, 1) and the accept uniform (block 2).
+template <class Model, class R>
+__device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n, R* z, R& u)
+{
+    constexpr int D = Model::D;
+#pragma unroll
+    for (int pair = 0; 2 * pair < D; ++pair) {
+        R z0, z1;
+        Num<R>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)n, kKindSite, pair), z0, z1);
+        z[2 * pair] = z0;
+        if (2 * pair + 1 < D) z[2 * pair + 1] = z1;
+    }
+    const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)n, kKindSite, 2u);
+    u = Num<R>::uni(w.x, w.y);
+}
+
+// One site move: proposal, f(x'), Delta A_n, Metropolis, store on accept.
+template <class Model, class R>
+__device__ __forceinline__ bool site_move(const Ctx& c, int64_t n, long long s, const R* pr, R beta,
+                                          R* Fc, unsigned long long& nonfinite)
+{
+    constexpr int D = Model::D;
+    R* X = (R*)c.X;
+    const R* sig = (const R*)c.sig;
+    R x[D], xp[D], fp[D], z[D], u;
+#pragma unroll
+    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    site_draws<Model, R>(c, s, n, z, u);
+#pragma unroll
+    for (int a = 0; a < D; ++a) xp[a] = x[a] + sig[a * c.ldx + n] * z[a];
+    const bool has_next = n < c.M;
+    if (has_next) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], R(c.dt), fp);
+    const R dA = site_delta<Model, R>(c, n, x, xp, fp, beta, Fc);
+    if (!isfinite(dA)) ++nonfinite;
+    const bool acc = metropolis<R>(dA, u);
+    if (acc) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) X[a * c.ldx + n] = xp[a];
+        if (has_next) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) Fc[a * c.ldf + n] = fp[a];
+        }
+        c.acc_win[n] += 1u;
+    }
+    return acc;
+}
+
+// Site n's share of a parameter move: f(x_n, p') into the inactive cache and
+// beta/2 sum_a Rf_a [(x_{n+1} - f')^2 - (x_{n+1} - f)^2].
+template <class Model, class R>
+__device__ __forceinline__ R param_term(const Ctx& c, int64_t n, const R* pq, R beta, const R* Fc, R* Fn)
+{
+    constexpr int D = Model::D;
+    const R* X = (const R*)c.X;
+    R x[D], fp[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    rk4_map<Model, R>(x, pq, ((const R*)c.I)[n], R(c.dt), fp);
+    R t = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        Fn[a * c.ldf + n] = fp[a];
+        const R xn1 = X[a * c.ldx + n + 1];
+        t += beta * sqdiff<R>(R(c.Rf[a]), xn1 - fp[a], xn1 - Fc[a * c.ldf + n]);
+    }
+    return t;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Fixed-order CTA sum; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* wsum)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) wsum[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kBlock / 32; ++k) t += wsum[k];
+    return t;
+}
+
+__device__ __forceinline__ int64_t hist_slot(double v, double lo, double hi, int nb)
+{
+    if (!(v >= lo)) return 0;
+    if (v >= hi) return nb + 1;
+    const double t = (v - lo) / (hi - lo);
+    int64_t b = (int64_t)floor(t * (double)nb);
+    if (b > nb - 1) b = nb - 1;
+    return 1 + b;
+}
+
+template <class Model, class R>
+__global__ void __launch_bounds__(kBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
+{
+    constexpr int D = Model::D, NP = Model::NP;
+    __shared__ SweepShared sh;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const DevState* g = c.st;
+        for (int l = 0; l < kMaxP; ++l) {
+            sh.p[l] = g->p[l]; sh.lo[l] = g->lo[l]; sh.hi[l] = g->hi[l]; sh.sigp[l] = g->sigp[l];
+            sh.accp_win[l] = g->accp_win[l]; sh.par_acc[l] = g->par_acc[l]; sh.par_prop[l] = g->par_prop[l];
+        }
+        sh.beta = g->beta; sh.sweep = g->sweep; sh.J = g->J; sh.fidx = g->fidx;
+        sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0;
+        sh.site_acc[0] = sh.site_acc[1] = sh.site_prop[0] = sh.site_prop[1] = sh.nonfinite = 0ull;
+    }
+    __syncthreads();
+
+    const int64_t M = c.M;
+    const int64_t n0 = (int64_t)blockIdx.x * c.tile;
+    const int64_t n1 = min(n0 + c.tile, M + 1);
+    const int64_t nx = (int64_t)D * (M + 1);
+    unsigned long long my_acc[2] = {0ull, 0ull}, my_prop[2] = {0ull, 0ull}, my_nf = 0ull;
+    R* X = (R*)c.X;
+    R* sig = (R*)c.sig;
+
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        const long long s = sh.sweep;
+        const R beta = R(sh.beta);
+        R pr[kMaxP];
+        Model::prep(sh.p, pr);
+
+        // ---- even then odd sites (Sec. 4.1) ----
+        for (int parity = 0; parity < 2; ++parity) {
+            R* Fc = (R*)c.F[sh.fidx];
+            const int64_t first = n0 + (((n0 & 1) != parity) ? 1 : 0);
+            for (int64_t n = first + 2 * (int64_t)tid; n < n1; n += 2 * kBlock) {
+                my_acc[parity] += site_move<Model, R>(c, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
+                my_prop[parity] += 1ull;
+            }
+            if (!grid_barrier(c, &sh.abort)) goto done;
+        }
+
+        // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
+        for (int l = 0; l < NP; ++l) {
+            if (!((sh.free_mask >> l) & 1u)) continue;
+            if (tid == 0) {
+                double z0, z1;
+                Num<double>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u), z0, z1);
+                const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
+                const double pl = sh.p[l] + sh.sigp[l] * z0;
+                sh.pnew = pl;
+                for (int q = 0; q < kMaxP; ++q) sh.pq[q] = sh.p[q];
+                sh.pq[l] = pl;
+                sh.uacc = u01d(w.x, w.y);
+                sh.inbox = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
+                sh.par_prop[l] += 1ull;
+            }
+            __syncthreads();
+            if (sh.inbox) {
+                R pq[kMaxP];
+                Model::prep(sh.pq, pq);
+                const R* Fc = (const R*)c.F[sh.fidx];
+                R* Fn = (R*)c.F[sh.fidx ^ 1u];
+                R part = R(0);
+                const int64_t nend = min(n1, M);
+                for (int64_t n = n0 + tid; n < nend; n += kBlock)
+                    part += param_term<Model, R>(c, n, pq, beta, Fc, Fn);
+                const double bs = block_sum((double)part, sh.wsum);
+                const unsigned slot = sh.nred & 1u;
+                if (tid == 0) c.partials[slot * kMaxGrid + blockIdx.x] = bs;
+                if (!grid_barrier(c, &sh.abort)) goto done;
+                if (tid < 32) {
+                    double v = 0.0;
+                    for (int i = tid; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
+                    v = warp_sum(v);
+                    if (tid == 0) {
+                        if (metropolis<double>(v, sh.uacc)) {
+                            sh.p[l] = sh.pnew;
+                            sh.fidx ^= 1u;
+                            sh.accp_win[l] += 1u;
+                            sh.par_acc[l] += 1ull;
+                        }
+                        sh.nred += 1u;
+                    }
+                }
+                __syncthreads();
+                Model::prep(sh.p, pr);
+            }
+            __syncthreads();
+        }
+
+        // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
+        const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
+        if (record) {
+            const bool first_rec = (sh.J == 0);
+            for (int64_t n = n0 + tid; n < n1; n += kBlock) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const double v = (double)X[a * c.ldx + n];
+                    const int64_t ci = (int64_t)a * (M + 1) + n;
+                    if (first_rec) c.shift[ci] = v;
+                    const double d = v - c.shift[ci];
+                    c.S1[ci] += d;
+                    c.S2[ci] += d * d;
+                }
+            }
+            if (blockIdx.x == 0 && tid < NP) {
+                const double v = sh.p[tid];
+                const int64_t ci = nx + tid;
+                if (first_rec) c.shift[ci] = v;
+                const double d = v - c.shift[ci];
+                c.S1[ci] += d;
+                c.S2[ci] += d * d;
+            }
+            for (int kk = tid; kk < c.n_sel; kk += kBlock) {
+                const int64_t ci = c.h_comp[kk];
+                double v;
+                bool mine;
+                if (ci < nx) {
+                    const int64_t a = ci / (M + 1), n = ci - a * (M + 1);
+                    mine = (n >= n0 && n < n1);
+                    v = mine ? (double)X[a * c.ldx + n] : 0.0;
+                } else {
+                    mine = (blockIdx.x == 0);
+                    v = sh.p[ci - nx];
+                }
+                if (mine) c.hist[(int64_t)kk * (c.n_bins + 2) + hist_slot(v, c.h_lo[kk], c.h_hi[kk], c.n_bins)] += 1ull;
+            }
+        }
+
+        // ---- step-size adaptation during burn-in (Sec. 4.2) ----
+        if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
+            for (int64_t n = n0 + tid; n < n1; n += kBlock) {
+                const double fac = 1.0 + c.alpha * ((double)c.acc_win[n] / (double)c.n_skip - c.f_acc);
+#pragma unroll
+                for (int a = 0; a < D; ++a) sig[a * c.ldx + n] = R((double)sig[a * c.ldx + n] * fac);
+                c.acc_win[n] = 0u;
+            }
+            if (tid == 0) {
+                for (int l = 0; l < NP; ++l) {
+                    if ((sh.free_mask >> l) & 1u)
+                        sh.sigp[l] *= 1.0 + c.alpha * ((double)sh.accp_win[l] / (double)c.n_skip - c.f_acc);
+                    sh.accp_win[l] = 0u;
+                }
+            }
+        }
+
+        // ---- annealing, Eq. (fbeta): beta_{s+1} = beta_s f_beta until N_cool ----
+        __syncthreads();
+        if (tid == 0) {
+            sh.beta = (s + 1 < c.n_cool) ? sh.beta * c.fbeta : 1.0;
+            sh.sweep = s + 1;
+            if (record) sh.J += 1;
+        }
+        __syncthreads();
+    }
+
+done:
+    __syncthreads();
+    atomicAdd(&sh.site_acc[0], my_acc[0]);
+    atomicAdd(&sh.site_acc[1], my_acc[1]);
+    atomicAdd(&sh.site_prop[0], my_prop[0]);
+    atomicAdd(&sh.site_prop[1], my_prop[1]);
+    atomicAdd(&sh.nonfinite, my_nf);
+    __syncthreads();
+    if (tid == 0) {
+        DevState* g = c.st;
+        atomicAdd(&g->site_acc[0], sh.site_acc[0]);
+        atomicAdd(&g->site_acc[1], sh.site_acc[1]);
+        atomicAdd(&g->site_prop[0], sh.site_prop[0]);
+        atomicAdd(&g->site_prop[1], sh.site_prop[1]);
+        atomicAdd(&g->nonfinite, sh.nonfinite);
+        if (blockIdx.x == 0) {
+            for (int l = 0; l < kMaxP; ++l) {
+                g->p[l] = sh.p[l]; g->sigp[l] = sh.sigp[l]; g->accp_win[l] = sh.accp_win[l];
+                g->par_acc[l] = sh.par_acc[l]; g->par_prop[l] = sh.par_prop[l];
+            }
+            g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx;
+        }
+    }
+}
+
+template <class Model, class R>
+static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s)
+{
+    Ctx cc = c;
+    int64_t ns = n_sweeps;
+    void* args[] = {(void*)&cc, (void*)&ns};
+    return cudaLaunchCooperativeKernel((const void*)sweep_kernel<Model, R>, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+template <class Model, class R>
+static int max_grid_t(int device)
+{
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Model, R>, kBlock, 0) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s)
+{
+    if (prec == 0) {
+        if (model == 0) return launch_sweep_t<HH<double>, double>(c, n_sweeps, grid, s);
+        if (model == 1) return launch_sweep_t<LinGauss<double>, double>(c, n_sweeps, grid, s);
+        return launch_sweep_t<Toy1D<double>, double>(c, n_sweeps, grid, s);
+    }
+    if (model == 0) return launch_sweep_t<HH<float>, float>(c, n_sweeps, grid, s);
+    if (model == 1) return launch_sweep_t<LinGauss<float>, float>(c, n_sweeps, grid, s);
+    return launch_sweep_t<Toy1D<float>, float>(c, n_sweeps, grid, s);
+}
+
+int sweep_max_grid(int model, int prec, int device)
+{
+    if (prec == 0) {
+        if (model == 0) return max_grid_t<HH<double>, double>(device);
+        if (model == 1) return max_grid_t<LinGauss<double>, double>(device);
+        return max_grid_t<Toy1D<double>, double>(device);
+    }
+    if (model == 0) return max_grid_t<HH<float>, float>(device);
+    if (model == 1) return max_grid_t<LinGauss<float>, float>(device);
+    return max_grid_t<Toy1D<float>, float>(device);
+}
+
+// ---- diagnostic kernels sharing the sweep's per-site code ------------------
+
+template <class Model, class R>
+__global__ void __launch_bounds__(kBlock) site_delta_kernel(Ctx c, const double* Xp, double beta, double* dA)
+{
+    constexpr int D = Model::D;
+    const int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (n > c.M) return;
+    const R* X = (const R*)c.X;
+    const R* Fc = (const R*)c.F[c.st->fidx];
+    R pr[kMaxP];
+    Model::prep(c.st->p, pr);
+    R x[D], xp[D], fp[D];
+    for (int a = 0; a < D; ++a) {
+        x[a] = X[a * c.ldx + n];
+        xp[a] = R(Xp[a * (c.M + 1) + n]);
+    }
+    if (n < c.M) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], R(c.dt), fp);
+    dA[n] = (double)site_delta<Model, R>(c, n, x, xp, fp, R(beta), Fc);
+}
+
+// Full-path parameter change of action: per-CTA sums in FP64, then the last
+// CTA to finish adds them in CTA order (single pass, deterministic).
+template <class Model, class R>
+__global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, double pl_new, double beta, double* out)
+{
+    __shared__ double wsum[kBlock / 32];
+    __shared__ int last;
+    const R* Fc = (const R*)c.F[c.st->fidx];
+    R* Fn = (R*)c.F[c.st->fidx ^ 1u];
+    double pd[kMaxP];
+    for (int q = 0; q < kMaxP; ++q) pd[q] = c.st->p[q];
+    pd[l] = pl_new;
+    R pq[kMaxP];
+    Model::prep(pd, pq);
+    R part = R(0);
+    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < c.M; n += (int64_t)gridDim.x * kBlock)
+        part += param_term<Model, R>(c, n, pq, R(beta), Fc, Fn);
+    const double bs = block_sum((double)part, wsum);
+    if (threadIdx.x == 0) {
+        c.red[blockIdx.x] = bs;
+        __threadfence();
+        last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(&c.red[i]);
+        *out = t;
+        *c.ticket = 0u;
+    }
+}
+
+template <class Model, class R>
+static cudaError_t site_delta_t(const Ctx& c, const double* Xp, double beta, double* dA, cudaStream_t s)
+{
+    const int grid = (int)((c.M + 1 + kBlock - 1) / kBlock);
+    site_delta_kernel<Model, R><<<grid, kBlock, 0, s>>>(c, Xp, beta, dA);
+    return cudaGetLastError();
+}
+
+template <class Model, class R>
+static cudaError_t param_delta_t(const Ctx& c, int l, double pl, double beta, double* out, cudaStream_t s)
+{
+    int grid = (int)((c.M + kBlock - 1) / kBlock);
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    if (grid < 1) grid = 1;
+    param_delta_kernel<Model, R><<<grid, kBlock, 0, s>>>(c, l, pl, beta, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_site_delta(int model, int prec, const Ctx& c, const double* Xp, double beta, double* dA,
+                              cudaStream_t s)
+{
+    if (prec == 0) {
+        if (model == 0) return site_delta_t<HH<double>, double>(c, Xp, beta, dA, s);
+        if (model == 1) return site_delta_t<LinGauss<double>, double>(c, Xp, beta, dA, s);
+        return site_delta_t<Toy1D<double>, double>(c, Xp, beta, dA, s);
+    }
+    if (model == 0) return site_delta_t<HH<float>, float>(c, Xp, beta, dA, s);
+    if (model == 1) return site_delta_t<LinGauss<float>, float>(c, Xp, beta, dA, s);
+    return site_delta_t<Toy1D<float>, float>(c, Xp, beta, dA, s);
+}
+
+cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double pl_new, double beta,
+                               double* out, cudaStream_t s)
+{
+    if (prec == 0) {
+        if (model == 0) return param_delta_t<HH<double>, double>(c, l, pl_new, beta, out, s);
+        if (model == 1) return param_delta_t<LinGauss<double>, double>(c, l, pl_new, beta, out, s);
+        return param_delta_t<Toy1D<double>, double>(c, l, pl_new, beta, out, s);
+    }
+    if (model == 0) return param_delta_t<HH<float>, float>(c, l, pl_new, beta, out, s);
+    if (model == 1) return param_delta_t<LinGauss<float>, float>(c, l, pl_new, beta, out, s);
+    return param_delta_t<Toy1D<float>, float>(c, l, pl_new, beta, out, s);
+}
+
+}  // namespace pimc

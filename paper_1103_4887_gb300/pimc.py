@@ -1,0 +1,306 @@
+"""Python binding of the C ABI in include/pimc.h (argument marshalling only).
+
+Every step of the sampler runs in the CUDA library ``_build/libpimc.so``; this
+module only converts numpy/torch arguments to pointers and error codes to
+exceptions.  There is no CPU fallback: without the built library every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32_MIXED = 0, 1
+MODEL_HH, MODEL_LINGAUSS, MODEL_TOY1D = 0, 1, 2
+MODEL_DIMS = {MODEL_HH: (4, 7), MODEL_LINGAUSS: (2, 1), MODEL_TOY1D: (1, 1)}
+
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
+_ERRNAMES = {ERR_ARG: "PIMC_ERR_ARG", ERR_STATE: "PIMC_ERR_STATE", ERR_CUDA: "PIMC_ERR_CUDA",
+             ERR_OOM: "PIMC_ERR_OOM", ERR_TIMEOUT: "PIMC_ERR_TIMEOUT", ERR_NUMERIC: "PIMC_ERR_NUMERIC",
+             ERR_IO: "PIMC_ERR_IO"}
+
+# Every symbol include/pimc.h declares (checked by the test suite).
+EXPORTS = [
+    "pimc_create", "pimc_destroy", "pimc_last_error", "pimc_set_stream", "pimc_set_precision",
+    "pimc_set_data", "pimc_load_data", "pimc_set_params", "pimc_set_path", "pimc_set_steps", "pimc_set_schedule",
+    "pimc_set_chain", "pimc_sweep", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
+    "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
+    "pimc_histograms", "pimc_histogram_shape", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
+    "pimc_launch_info", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
+    "pimc_debug_skip_arrive", "pimc_set_grid",
+]
+
+
+class PimcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_d = ctypes.c_double
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (fails loudly when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _build.LIB
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA sampler library not built ({p}); run __graft_entry__.build()")
+            L = ctypes.CDLL(p)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    sig = {
+        "pimc_create": [_vp, _int, _i64, _int, _int, _d, _vp, _vp],
+        "pimc_destroy": [_vp],
+        "pimc_set_stream": [_vp, _vp],
+        "pimc_set_precision": [_vp, _int],
+        "pimc_set_data": [_vp, _vp, _vp],
+        "pimc_load_data": [_vp, _vp, _vp],
+        "pimc_set_params": [_vp, _vp, _vp, _vp, _vp, _int],
+        "pimc_set_path": [_vp, _vp],
+        "pimc_set_steps": [_vp, _vp, _int, _vp],
+        "pimc_set_schedule": [_vp, _i64, _i64, _d, _i64, _d, _d],
+        "pimc_set_chain": [_vp, ctypes.c_uint32],
+        "pimc_sweep": [_vp, _i64, ctypes.c_uint64],
+        "pimc_sync": [_vp],
+        "pimc_action": [_vp, _vp, _vp, _vp],
+        "pimc_grad": [_vp, _d, _vp, _vp],
+        "pimc_action_dev": [_vp, _vp, _vp, _vp, _vp],
+        "pimc_grad_dev": [_vp, _vp, _vp, _d, _vp, _vp, _vp],
+        "pimc_site_delta": [_vp, _vp, _d, _vp],
+        "pimc_param_delta": [_vp, _int, _d, _d, _vp],
+        "pimc_moments": [_vp, _vp, _vp, _vp],
+        "pimc_set_histograms": [_vp, _int, _vp, _vp, _vp, _int],
+        "pimc_histograms": [_vp, _vp],
+        "pimc_histogram_shape": [_vp, _vp, _vp],
+        "pimc_get_state": [_vp, _vp, _vp],
+        "pimc_get_steps": [_vp, _vp, _vp],
+        "pimc_get_sweep": [_vp, _vp, _vp],
+        "pimc_accept_stats": [_vp, _vp, _vp, _vp, _vp],
+        "pimc_launch_info": [_vp, _vp, _vp],
+        "pimc_checkpoint_save": [_vp, ctypes.c_char_p],
+        "pimc_checkpoint_load": [_vp, ctypes.c_char_p],
+        "pimc_set_wait_limit": [_vp, _i64],
+        "pimc_debug_skip_arrive": [_vp, _int],
+        "pimc_set_grid": [_vp, _int],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _int
+    L.pimc_last_error.argtypes = [_vp]
+    L.pimc_last_error.restype = ctypes.c_char_p
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Sampler:
+    """Handle of the GPU sampler for one chain over one data set."""
+
+    def __init__(self, model, M, dt, Rm, Rf, precision=FP64):
+        self._L = load()
+        self.model = int(model)
+        self.D, self.Np = MODEL_DIMS[self.model]
+        self.M = int(M)
+        h = ctypes.c_void_p()
+        rm = np.array([float(Rm)])
+        rf = _f64(Rf)
+        r = self._L.pimc_create(ctypes.byref(h), self.model, self.M, self.D, 1, float(dt), _p(rm), _p(rf))
+        if r != OK:
+            raise PimcError(r, self._L.pimc_last_error(None).decode())
+        self._h = h
+        if precision != FP64:
+            self.set_precision(precision)
+
+    @classmethod
+    def from_problem(cls, prob, precision=FP64):
+        s = cls(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf, precision)
+        s.set_data(prob.y, prob.I)
+        s.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+        s.set_steps(prob.sig_x, prob.sig_p)
+        return s
+
+    def _ck(self, r):
+        if r != OK:
+            raise PimcError(r, self._L.pimc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pimc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setup
+    def set_stream(self, stream_ptr):
+        self._ck(self._L.pimc_set_stream(self._h, ctypes.c_void_p(int(stream_ptr))))
+
+    def set_precision(self, precision):
+        self._ck(self._L.pimc_set_precision(self._h, int(precision)))
+
+    def set_data(self, y, I):
+        self._ck(self._L.pimc_set_data(self._h, _p(_f64(y)), _p(_f64(I))))
+
+    def load_data(self, y_ptr, I_ptr):
+        """New data (host pointers, e.g. pinned tensors) for the running chain."""
+        self._ck(self._L.pimc_load_data(self._h, _vp(y_ptr), _vp(I_ptr)))
+
+    def set_params(self, p, lo=None, hi=None, free=None):
+        fr = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
+        self._ck(self._L.pimc_set_params(self._h, _p(_f64(p)), _p(None if lo is None else _f64(lo)),
+                                         _p(None if hi is None else _f64(hi)), _p(fr), self.Np))
+
+    def set_path(self, X=None):
+        self._ck(self._L.pimc_set_path(self._h, _p(None if X is None else _f64(X).reshape(-1))))
+
+    def set_steps(self, sig_x, sig_p):
+        sx = _f64(sig_x).reshape(-1)
+        per_site = 1 if sx.size == self.D * (self.M + 1) else 0
+        self._ck(self._L.pimc_set_steps(self._h, _p(sx), per_site, _p(_f64(sig_p))))
+
+    def set_schedule(self, n_init=0, n_skip=1, beta0=1.0, n_cool=0, f_acc=0.4, alpha=0.0):
+        self._ck(self._L.pimc_set_schedule(self._h, int(n_init), int(n_skip), float(beta0), int(n_cool),
+                                           float(f_acc), float(alpha)))
+
+    def set_chain(self, chain):
+        self._ck(self._L.pimc_set_chain(self._h, int(chain)))
+
+    def set_grid(self, grid):
+        self._ck(self._L.pimc_set_grid(self._h, int(grid)))
+
+    def set_wait_limit(self, ns):
+        self._ck(self._L.pimc_set_wait_limit(self._h, int(ns)))
+
+    def debug_skip_arrive(self, cta):
+        self._ck(self._L.pimc_debug_skip_arrive(self._h, int(cta)))
+
+    # ---- run
+    def sweep(self, n, seed, sync=True):
+        self._ck(self._L.pimc_sweep(self._h, int(n), int(seed)))
+        if sync:
+            self.sync()
+
+    def sync(self):
+        self._ck(self._L.pimc_sync(self._h))
+
+    # ---- queries
+    def action(self):
+        a = np.zeros(3)
+        self._ck(self._L.pimc_action(self._h, _p(a[0:1]), _p(a[1:2]), _p(a[2:3])))
+        return float(a[0]), float(a[1]), float(a[2])
+
+    def grad(self, beta=1.0):
+        gX = np.zeros(self.D * (self.M + 1))
+        gp = np.zeros(self.Np)
+        self._ck(self._L.pimc_grad(self._h, float(beta), _p(gX), _p(gp)))
+        return gX.reshape(self.D, self.M + 1), gp
+
+    def action_dev(self, X_ptr, p_ptr, out_ptr, stream_ptr):
+        self._ck(self._L.pimc_action_dev(self._h, _vp(X_ptr), _vp(p_ptr), _vp(out_ptr), _vp(stream_ptr)))
+
+    def grad_dev(self, X_ptr, p_ptr, beta, gX_ptr, gp_ptr, stream_ptr):
+        self._ck(self._L.pimc_grad_dev(self._h, _vp(X_ptr), _vp(p_ptr), float(beta), _vp(gX_ptr),
+                                       _vp(gp_ptr), _vp(stream_ptr)))
+
+    def site_delta(self, Xp, beta=1.0):
+        out = np.zeros(self.M + 1)
+        self._ck(self._L.pimc_site_delta(self._h, _p(_f64(Xp).reshape(-1)), float(beta), _p(out)))
+        return out
+
+    def param_delta(self, l, pl_new, beta=1.0):
+        out = np.zeros(1)
+        self._ck(self._L.pimc_param_delta(self._h, int(l), float(pl_new), float(beta), _p(out)))
+        return float(out[0])
+
+    def moments(self):
+        nc = self.D * (self.M + 1) + self.Np
+        mean = np.zeros(nc)
+        var = np.zeros(nc)
+        J = np.zeros(1, dtype=np.int64)
+        self._ck(self._L.pimc_moments(self._h, _p(mean), _p(var), _p(J)))
+        return mean, var, int(J[0])
+
+    def set_histograms(self, comp, lo, hi, n_bins):
+        comp = np.ascontiguousarray(comp, dtype=np.int64)
+        self._ck(self._L.pimc_set_histograms(self._h, comp.size, _p(comp), _p(_f64(lo)), _p(_f64(hi)),
+                                             int(n_bins)))
+
+    def histograms(self):
+        ns, nb = ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.pimc_histogram_shape(self._h, ctypes.byref(ns), ctypes.byref(nb)))
+        out = np.zeros(ns.value * (nb.value + 2), dtype=np.uint64)
+        self._ck(self._L.pimc_histograms(self._h, _p(out)))
+        return out.reshape(ns.value, nb.value + 2)
+
+    def state(self):
+        X = np.zeros(self.D * (self.M + 1))
+        p = np.zeros(self.Np)
+        self._ck(self._L.pimc_get_state(self._h, _p(X), _p(p)))
+        return X.reshape(self.D, self.M + 1), p
+
+    def params(self):
+        p = np.zeros(self.Np)
+        self._ck(self._L.pimc_get_state(self._h, None, _p(p)))
+        return p
+
+    def steps(self):
+        sx = np.zeros(self.D * (self.M + 1))
+        sp = np.zeros(self.Np)
+        self._ck(self._L.pimc_get_steps(self._h, _p(sx), _p(sp)))
+        return sx.reshape(self.D, self.M + 1), sp
+
+    def sweep_counter(self):
+        s = np.zeros(1, dtype=np.int64)
+        b = np.zeros(1)
+        self._ck(self._L.pimc_get_sweep(self._h, _p(s), _p(b)))
+        return int(s[0]), float(b[0])
+
+    def accept_stats(self):
+        sa = np.zeros(2, dtype=np.uint64)
+        sp = np.zeros(2, dtype=np.uint64)
+        pa = np.zeros(self.Np, dtype=np.uint64)
+        pp = np.zeros(self.Np, dtype=np.uint64)
+        self._ck(self._L.pimc_accept_stats(self._h, _p(sa), _p(sp), _p(pa), _p(pp)))
+        return sa, sp, pa, pp
+
+    def launch_info(self):
+        g = ctypes.c_int()
+        b = ctypes.c_int()
+        self._ck(self._L.pimc_launch_info(self._h, ctypes.byref(g), ctypes.byref(b)))
+        return g.value, b.value
+
+    def checkpoint_save(self, path):
+        self._ck(self._L.pimc_checkpoint_save(self._h, os.fsencode(path)))
+
+    def checkpoint_load(self, path):
+        self._ck(self._L.pimc_checkpoint_load(self._h, os.fsencode(path)))
