@@ -139,6 +139,20 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """Three single-sweep launches of the sweep kernel in each precision on the
+    bench workload (no timing); the case the ncu captures use."""
+    from paper_1103_4887_gb300 import pimc, synth
+    prob = synth.hh_problem(args.M, data_seed=0, free="all")
+    for prec in (pimc.FP32_MIXED, pimc.FP64):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_schedule(n_init=0, n_skip=NSKIP)
+        for _ in range(3):
+            s.sweep(1, SEED)
+        s.close()
+    print("profile case done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,10 +163,15 @@ def main():
     ap.add_argument("--M", type=int, default=M_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=40)
+    ap.add_argument("--profile", action="store_true",
+                    help="no timing: 3 single-sweep launches per precision (a small case for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile:
+        run_profile_case(args)
         return
 
     import torch
