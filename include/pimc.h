@@ -149,6 +149,29 @@ int pimc_action_dev(pimc_t h, const double* X_dev, const double* p_dev, double* 
 int pimc_grad_dev(pimc_t h, const double* X_dev, const double* p_dev, double beta,
                   double* gX_dev, double* gp_dev, void* stream);
 
+/* Allocation-free action.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they call --
+ * code held to a fixed memory budget or a caller-owned pool, plugin hosts
+ * that forbid cudaMalloc/cudaFree on their threads, and real-time loops in
+ * which an allocation (which may synchronise the device) is not allowed.
+ * It computes the same FP64 action (A, A_o, A_f at beta = 1) as
+ * pimc_action_dev, without a handle: X_dev (D*(M+1) doubles, SoA), p_dev
+ * (Np), y_dev (M+1), I_dev (M) and out_dev (3 doubles) are caller-owned
+ * device arrays, Rf (D doubles) is host memory; work is enqueued on `stream`.
+ * Its scratch (per-CTA partial sums and a last-block counter, 33,024 bytes)
+ * is one fixed array in device memory that every GPU loading this library
+ * holds until the process exits, so M is limited to 1 <= M <= 262,143;
+ * larger M (and bad pointers or sizes) return PIMC_ERR_ARG with a message in
+ * pimc_last_error(NULL).  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The first call on a device looks up the array's
+ * device address on that device (make that first call before any stream
+ * capture).  Every call shares the array: calls that overlap on the GPU
+ * (different streams, devices excepted) race and must be serialised by the
+ * caller. */
+int pimc_action_static(int model, int64_t M, double dt, double Rm, const double* Rf,
+                       const double* X_dev, const double* p_dev, const double* y_dev,
+                       const double* I_dev, double* out_dev, void* stream);
+
 /* ---- diagnostics of the hot path (parity tests) ------------------------------ */
 
 /* Local change of action Delta A_n for replacing x_n by Xp[:,n], each site

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpimc.so")
 ROOT = os.path.dirname(HERE)
 
-CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu"]
+CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu", "noalloc.cu"]
 HEADERS = ["device.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

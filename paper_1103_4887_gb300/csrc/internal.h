@@ -58,6 +58,9 @@ struct Ctx {
     int64_t tile;                 // sites per CTA in the sweep kernel
 };
 
+// Message returned by pimc_last_error(NULL) on this thread.
+void set_thread_error(const char* msg);
+
 // Kernel launchers (model: pimc_model, prec: pimc_precision).
 cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s);
 int sweep_max_grid(int model, int prec, int device);  // co-resident CTAs on the device

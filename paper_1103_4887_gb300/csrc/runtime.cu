@@ -222,6 +222,8 @@ int reset_stats(pimc_t h)
 
 }  // namespace
 
+void pimc::set_thread_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, const double* Rm, const double* Rf)

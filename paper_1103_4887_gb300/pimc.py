@@ -32,7 +32,7 @@ EXPORTS = [
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
-    "pimc_debug_skip_arrive", "pimc_set_grid",
+    "pimc_debug_skip_arrive", "pimc_set_grid", "pimc_action_static",
 ]
 
 
@@ -103,6 +103,7 @@ def _declare(L):
         "pimc_set_wait_limit": [_vp, _i64],
         "pimc_debug_skip_arrive": [_vp, _int],
         "pimc_set_grid": [_vp, _int],
+        "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -118,6 +119,16 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def action_static(model, M, dt, Rm, Rf, X_ptr, p_ptr, y_ptr, I_ptr, out_ptr, stream_ptr):
+    """Allocation-free FP64 action of caller-owned device arrays (no handle)."""
+    L = load()
+    rf = _f64(Rf)
+    r = L.pimc_action_static(int(model), int(M), float(dt), float(Rm), _p(rf), _vp(X_ptr), _vp(p_ptr),
+                             _vp(y_ptr), _vp(I_ptr), _vp(out_ptr), _vp(stream_ptr))
+    if r != OK:
+        raise PimcError(r, L.pimc_last_error(None).decode())
 
 
 class Sampler:
