@@ -20,7 +20,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
@@ -49,19 +48,38 @@ def maps_per_sweep(M, n_free):
     return M * (1 + n_free)
 
 
-def gpu_clock_sampler(stop, out):
-    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-           "--format=csv,noheader,nounits", "-i", str(out["index"])]
-    while not stop.is_set():
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while active."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
         try:
-            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
-            if r.returncode == 0 and r.stdout.strip():
-                out["rows"].append([c.strip() for c in r.stdout.strip().split(",")])
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
-            pass
-        stop.wait(0.2)
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is not None:
+            time.sleep(0.06)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.rows = [[c.strip() for c in ln.split(",")] for ln in out.splitlines() if ln.strip()]
+        return False
 
 
 def summarize_clocks(rows):
@@ -153,10 +171,124 @@ def run_profile_case(args):
     print("profile case done")
 
 
+def _peak_fp32_tflops(n_sm, sm_mhz):
+    t_map = max(FP32_OPS_PER_MAP / (n_sm * 128 * sm_mhz * 1e6), MUFU_OPS_PER_MAP / (n_sm * 16 * sm_mhz * 1e6))
+    return FLOP_PER_MAP / t_map / 1e12
+
+
+def run_sweep_M(args):
+    """Observation-length sweep (HH, all 7 parameters free): per M, device time
+    per sweep in one persistent launch (state L2-resident between sweeps, as in
+    a sampling run), FP32-mixed and FP64, and the serial oracle on one host core
+    for a bounded number of sweeps."""
+    import torch
+    import oracle
+    from paper_1103_4887_gb300 import pimc, synth
+    peaks, _ = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    for e in range(10, 21, 2):
+        M = 1 << e
+        prob = synth.hh_problem(M, data_seed=0, free="all")
+        row = {"M": M}
+        for name, prec, n in (("fp32mixed", pimc.FP32_MIXED, 400 if M <= 1 << 16 else 100),
+                              ("fp64", pimc.FP64, 40 if M <= 1 << 16 else 10)):
+            s = pimc.Sampler.from_problem(prob, precision=prec)
+            s.set_schedule(n_init=0, n_skip=NSKIP)
+            s.sweep(5, SEED)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st = torch.cuda.current_stream()
+            s.set_stream(st.cuda_stream)
+            e0.record(st)
+            s.sweep(n, SEED, sync=False)
+            e1.record(st)
+            torch.cuda.synchronize()
+            s.sync()
+            ms = e0.elapsed_time(e1) / n
+            maps = maps_per_sweep(M, 7)
+            tf = maps * FLOP_PER_MAP / (ms * 1e-3) / 1e12
+            peak = _peak_fp32_tflops(n_sm, sm_mhz) if prec == pimc.FP32_MIXED else 1.25
+            row[name] = {"ms_per_sweep": ms, "site_updates_per_s": (M + 1) / (ms * 1e-3),
+                         "rk4_maps_per_s": maps / (ms * 1e-3), "achieved_tflops": tf, "roofline_frac": tf / peak,
+                         "grid_block": list(s.launch_info())}
+            s.close()
+        ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+        ch.set_data(prob.y, prob.I)
+        ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+        ch.set_steps(prob.sig_x, prob.sig_p)
+        n_cpu = 100 if M <= 1 << 12 else (10 if M <= 1 << 16 else 2)
+        t0 = time.perf_counter()
+        ch.sweep(n_cpu, SEED)
+        cpu_s = (time.perf_counter() - t0) / n_cpu
+        row["oracle_1core"] = {"s_per_sweep": cpu_s, "site_updates_per_s": (M + 1) / cpu_s, "sweeps_timed": n_cpu}
+        row["speedup_fp32_vs_oracle"] = cpu_s / (row["fp32mixed"]["ms_per_sweep"] * 1e-3)
+        row["speedup_fp64_vs_oracle"] = cpu_s / (row["fp64"]["ms_per_sweep"] * 1e-3)
+        print(json.dumps(row), flush=True)
+
+
+def run_ess(args):
+    """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
+    all 7 parameters free): checkerboard Metropolis in FP32-mixed and FP64, and
+    whole-path HMC (FP64), each after an adaptive burn-in, on the same data."""
+    import torch
+    from paper_1103_4887_gb300 import diagnostics, pimc, synth
+    M = 16384
+    prob = synth.hh_problem(M, data_seed=0, free="all")
+    out = {"M": M, "n_free": 7}
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 20000),
+                                ("metropolis_fp64", pimc.FP64, 2000, 4000)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_stream(st.cuda_stream)
+        s.set_schedule(n_init=burn, n_skip=20, f_acc=0.4, alpha=0.5)
+        s.sweep(burn, SEED, sync=False)
+        s.set_param_trace(n)
+        secs = timed(lambda: s.sweep(n, SEED, sync=False))
+        s.sync()
+        tr = s.param_trace()
+        ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
+        out[name] = {"sweeps": n, "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
+                     "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
+        s.close()
+
+    # whole-path HMC: diagonal mass from burn-in variances, step tuned to ~70 %
+    s = pimc.Sampler.from_problem(prob, precision=pimc.FP64)
+    s.set_stream(st.cuda_stream)
+    s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
+    s.sweep(4000, SEED, sync=False)
+    mean, var, J = s.moments()
+    inv_mass = np.where(np.isfinite(var) & (var > 0), var, 1e-12)
+    s.set_schedule(n_init=10 ** 9, n_skip=1)
+    eps, n_leap = 0.05, 20
+    for _ in range(12):
+        acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
+        eps *= float(np.exp(1.5 * (acc - 0.7)))
+    n_traj = 1500
+    s.set_param_trace(n_traj)
+    acc_box = {}
+    secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
+    tr = s.param_trace()
+    ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
+    out["hmc_fp64"] = {"trajectories": n_traj, "n_leap": n_leap, "eps": eps, "accept": acc_box["n"] / n_traj,
+                       "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
+                       "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
+    s.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32mixed", choices=["fp32mixed", "fp64"])
@@ -165,6 +297,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
                     help="no timing: 3 single-sweep launches per precision (a small case for ncu)")
+    ap.add_argument("--sweep-M", action="store_true",
+                    help="observation-length sweep M = 2^10..2^20: site-updates/s and roofline per M, FP32-mixed "
+                         "and FP64, with the serial oracle timed on the host for the same M")
+    ap.add_argument("--ess", action="store_true",
+                    help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -172,6 +309,12 @@ def main():
         return
     if args.profile:
         run_profile_case(args)
+        return
+    if args.sweep_M:
+        run_sweep_M(args)
+        return
+    if args.ess:
+        run_ess(args)
         return
 
     import torch
@@ -221,13 +364,8 @@ def main():
         return [e0.elapsed_time(e1) for e0, e1 in evs]
 
     # clocks during the timed region
-    clk = {"index": local, "rows": []}
-    stop = threading.Event()
-    th = threading.Thread(target=gpu_clock_sampler, args=(stop, clk), daemon=True)
-    th.start()
-    ms = timed_steps(samp, args.steps, args.warmup)
-    stop.set()
-    th.join(timeout=10)
+    with ClockSampler(local) as clk:
+        ms = timed_steps(samp, args.steps, args.warmup)
     total_ms = sum(ms)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -302,7 +440,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every timed sweep",
                            "grid_block": list(samp.launch_info())},
                 "gpu_launches": args.steps,
-                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk["rows"]),
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk.rows),
                 "steady_state": steady, "fp64": fp64}
         print(json.dumps(line))
     if dist is not None:

@@ -130,6 +130,23 @@ int pimc_set_chain(pimc_t h, uint32_t chain);
  * Philox-4x32-10 keyed by `seed` with counters (n or l, sweep, kind, chain),
  * so a run resumes exactly at the handle's sweep counter.  Asynchronous. */
 int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed);
+/* Whole-path Hybrid Monte Carlo: n_traj trajectories, each moving X and the
+ * free parameters together by n_leap leapfrog steps of the Hamiltonian
+ * H = A + 1/2 P^T diag(inv_mass) P (beta = 1), with the step jittered
+ * uniformly in [0.8, 1.2] eps per trajectory and the usual accept test
+ * (Eq. (Paccept) on Delta H).  The gradient is the reverse-mode adjoint of
+ * the action through the RK4 map (pimc_grad).  inv_mass: D*(M+1)+Np host
+ * doubles (NULL: all ones; entries of fixed parameters are ignored).  A
+ * trajectory that takes a parameter out of its box is rejected.  Momenta and
+ * uniforms are Philox draws keyed by (component pair | 0, trajectory, kind 2 |
+ * 3, chain) with the trajectory counter = the sweep counter, which advances by
+ * one per trajectory; statistics follow the schedule of pimc_set_schedule.
+ * The launch sequence of one trajectory is captured once as a CUDA graph on
+ * the handle's stream and replayed.  *n_accepted (may be NULL; if not NULL the
+ * call synchronises) receives the accepted count of this call. */
+int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv_mass, uint64_t seed,
+             int64_t* n_accepted);
+
 /* Synchronise and return the sticky device status (PIMC_ERR_TIMEOUT if a
  * bounded wait expired in any launch since the last call; the flag is cleared). */
 int pimc_sync(pimc_t h);
@@ -194,6 +211,15 @@ int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const do
 int pimc_histograms(pimc_t h, uint64_t* counts);
 /* Current histogram configuration (0, 0 when none is set). */
 int pimc_histogram_shape(pimc_t h, int* n_sel, int* n_bins);
+
+/* Parameter trace: after every sweep the kernel writes p into a device ring
+ * of `cap` vectors (0 disables).  Resets the trace.  For effective-sample-
+ * size diagnostics of the parameter chain. */
+int pimc_set_param_trace(pimc_t h, int64_t cap);
+/* The last min(n, ring capacity, cap) parameter vectors in chronological
+ * order, Np doubles each; *n_written receives that count (out may be NULL to
+ * query it). */
+int pimc_param_trace(pimc_t h, double* out, int64_t cap, int64_t* n_written);
 
 /* ---- state ----------------------------------------------------------------- */
 int pimc_get_state(pimc_t h, double* X, double* p);

@@ -16,8 +16,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpimc.so")
 ROOT = os.path.dirname(HERE)
 
-CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu", "noalloc.cu"]
-HEADERS = ["device.cuh", "internal.h"]
+CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu", "noalloc.cu", "hmc.cu"]
+HEADERS = ["device.cuh", "internal.h", "stats.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

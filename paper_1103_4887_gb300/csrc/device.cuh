@@ -99,6 +99,17 @@ template <class R> __device__ __forceinline__ R psi(R u)
     if (fabs(u) < Num<R>::psi_cut) return R(1) + u * (R(0.5) + u * R(1.0 / 12.0));
     return Num<R>::div(-u, Num<R>::exm1(-u));
 }
+// psi(u) as a quotient num/den: (u, 1 - e^{-u}), or (series, 1) below the cut.
+template <class R> __device__ __forceinline__ void psi_frac(R u, R& num, R& den)
+{
+    if (fabs(u) < Num<R>::psi_cut) {
+        num = R(1) + u * (R(0.5) + u * R(1.0 / 12.0));
+        den = R(1);
+    } else {
+        num = u;
+        den = -Num<R>::exm1(-u);
+    }
+}
 // d psi/du = (1 - e^{-u} - u e^{-u}) / (1 - e^{-u})^2; series
 // 1/2 + u/6 - u^3/180 + u^5/5040 below the cut.
 template <class R> __device__ __forceinline__ R dpsi(R u)
@@ -126,15 +137,27 @@ template <class R> struct HH {
         for (int l = 0; l < NP; ++l) q[l] = R(p[l]);
         q[7] = R(1.0 / p[6]);
     }
-    // Rates in 1/ms, V in mV; divisions by constants written as products.
+    // Rates in 1/ms, V in mV.  With t = V + 65 and E = e^{-t/80}:
+    // beta_n = 0.125 E, alpha_h = 0.07 E^4 (= 0.07 e^{-t/20}),
+    // beta_h = 1/(1 + E^8 e^3) (= 1/(1 + e^{-(V+35)/10})), beta_m = 4 e^{-t/18};
+    // alpha_m = psi((V+40)/10), alpha_n = 0.1 psi((V+55)/10).  The three
+    // quotients share one reciprocal.  Divisions by constants are products.
     static __device__ __forceinline__ void rates(R V, R a[3], R b[3])
     {
-        a[0] = psi<R>((V + R(40)) * R(0.1));
-        b[0] = R(4) * Num<R>::ex((V + R(65)) * R(-1.0 / 18.0));
-        a[1] = R(0.07) * Num<R>::ex((V + R(65)) * R(-0.05));
-        b[1] = Num<R>::div(R(1), R(1) + Num<R>::ex((V + R(35)) * R(-0.1)));
-        a[2] = R(0.1) * psi<R>((V + R(55)) * R(0.1));
-        b[2] = R(0.125) * Num<R>::ex((V + R(65)) * R(-0.0125));
+        const R t = V + R(65);
+        const R E = Num<R>::ex(t * R(-0.0125));
+        const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
+        b[2] = R(0.125) * E;
+        a[1] = R(0.07) * E4;
+        b[0] = R(4) * Num<R>::ex(t * R(-1.0 / 18.0));
+        R nm, dm, nn, dn;
+        psi_frac<R>((V + R(40)) * R(0.1), nm, dm);
+        psi_frac<R>((V + R(55)) * R(0.1), nn, dn);
+        const R dh = R(1) + E8 * R(20.085536923187668);  // e^3
+        const R r = Num<R>::div(R(1), dm * dn * dh);
+        a[0] = nm * (dn * dh * r);
+        a[2] = R(0.1) * nn * (dm * dh * r);
+        b[1] = dm * dn * r;
     }
     static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F)
     {
@@ -228,6 +251,12 @@ template <class R> struct Toy1D {
     static __device__ __forceinline__ void init_site(R V, R* x) { x[0] = V; }
 };
 
+// pimc_model value of each model type.
+template <class Model> struct ModelId;
+template <class R> struct ModelId<HH<R>> { static constexpr int value = 0; };
+template <class R> struct ModelId<LinGauss<R>> { static constexpr int value = 1; };
+template <class R> struct ModelId<Toy1D<R>> { static constexpr int value = 2; };
+
 // One classical RK4 step of size dt with the drive held at I:
 // f = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).
 template <class Model, class R>
@@ -303,6 +332,12 @@ template <class R> __device__ __forceinline__ R sqdiff(R Rw, R dp, R d)
 {
     return R(0.5) * Rw * (dp - d) * (dp + d);
 }
+
+// Metropolis rule written with E = -log(u), which can be formed before dA is
+// known: u < exp(-dA) <=> dA < E (and dA <= 0 < E); NaN compares false.
+template <class R> __device__ __forceinline__ R neglog(R u);
+template <> __device__ __forceinline__ double neglog<double>(double u) { return -log(u); }
+template <> __device__ __forceinline__ float neglog<float>(float u) { return -__logf(u); }
 
 // Metropolis rule, Eq. (Paccept): accept iff dA <= 0 or u < exp(-dA);
 // a non-finite dA is a rejection.

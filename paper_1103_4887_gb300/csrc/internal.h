@@ -7,7 +7,8 @@
 
 namespace pimc {
 
-constexpr int kBlock = 128;          // threads per CTA of every kernel
+constexpr int kBlock = 128;          // threads per CTA of the whole-path kernels
+constexpr int kSweepBlock = 256;     // threads per CTA of the sweep kernel
 constexpr int kMaxParams = 8;
 constexpr int kMaxGrid = 4096;       // upper bound on CTAs of a launch (partials capacity)
 constexpr int kMaxSel = 64;          // histogram components
@@ -23,6 +24,7 @@ struct DevState {
     unsigned fidx, free_mask;
     unsigned accp_win[8];
     unsigned long long site_acc[2], site_prop[2], par_acc[8], par_prop[8], nonfinite;
+    long long tr_n;  // parameter vectors written to the trace ring so far
     int status;   // sticky error bits (kStatusTimeout)
     int abort;    // set by a CTA whose bounded wait expired; all CTAs leave
 };
@@ -49,6 +51,8 @@ struct Ctx {
     const int64_t* h_comp;
     const double *h_lo, *h_hi;
     int n_sel, n_bins;
+    double* trace;                // [trace_cap][NP] ring of p after each sweep (or null)
+    int64_t trace_cap;
     int64_t n_init, n_skip, n_cool;
     double fbeta, f_acc, alpha;
     uint64_t seed;
@@ -57,6 +61,24 @@ struct Ctx {
     int skip_cta;
     int64_t tile;                 // sites per CTA in the sweep kernel
 };
+
+// Device-side scalars of one HMC trajectory.
+struct HmcScalars {
+    double A0[3], A1[3];          // action (A, A_o, A_f) at the start and end
+    double K0, K1, dH, E, eps;    // kinetic energies, dH, -log u, jittered step
+    int oob, accept;
+    unsigned long long n_acc, n_traj;
+};
+struct HmcBuffers {
+    HmcScalars* hs;
+    double *Q, *P, *g, *invm;     // [D*(M+1) + NP] each: positions, momenta, gradient, inverse mass
+};
+cudaError_t launch_hmc_trajectory(int model, int prec, const Ctx& c, const HmcBuffers& b, int n_leap, double eps,
+                                  uint64_t seed, cudaStream_t s);
+
+template <class R> constexpr int prec_of();
+template <> constexpr int prec_of<double>() { return 0; }
+template <> constexpr int prec_of<float>() { return 1; }
 
 // Message returned by pimc_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);

@@ -40,6 +40,15 @@ struct pimc_handle_s {
     int n_sel = 0, n_bins = 0;
     double* dense = nullptr;  // D*(M+1) FP64 staging
     double* small = nullptr;  // 16 doubles of results
+    HmcBuffers hmc{};         // HMC state (allocated on first use)
+    cudaGraphExec_t hmc_exec = nullptr;
+    int hmc_leap = -1;
+    double hmc_eps = 0.0;
+    uint64_t hmc_seed = 0;
+    int hmc_prec = -1;
+    unsigned ctx_version = 0, hmc_version = ~0u;  // settings captured into the HMC graph
+    double* trace = nullptr;  // parameter trace ring [trace_cap][NP]
+    int64_t trace_cap = 0;
     double* y64 = nullptr;    // FP64 copies of the data as given (M+1, M)
     double* I64 = nullptr;
     bool have_data = false, have_params = false;
@@ -94,6 +103,7 @@ Ctx make_ctx(pimc_t h)
     c.S1 = h->S1; c.S2 = h->S2; c.shift = h->shift;
     c.hist = h->hist; c.h_comp = h->h_comp; c.h_lo = h->h_lo; c.h_hi = h->h_hi;
     c.n_sel = h->n_sel; c.n_bins = h->n_bins;
+    c.trace = h->trace; c.trace_cap = h->trace_cap;
     c.n_init = h->n_init; c.n_skip = h->n_skip; c.n_cool = h->n_cool;
     c.fbeta = h->fbeta; c.f_acc = h->f_acc; c.alpha = h->alpha;
     c.chain = h->chain; c.wait_ns = h->wait_ns; c.skip_cta = h->skip_cta;
@@ -183,7 +193,7 @@ void choose_grid(pimc_t h)
         g = h->grid_override;
     } else {
         const int64_t by_sm = std::min<int64_t>(h->num_sms, (sites + 63) / 64);
-        const int64_t by_threads = (sites + 2 * kBlock - 1) / (2 * kBlock);
+        const int64_t by_threads = (sites + 2 * kSweepBlock - 1) / (2 * kSweepBlock);
         g = std::max<int64_t>(by_sm, by_threads);
     }
     if (g > maxco) g = maxco;
@@ -203,9 +213,11 @@ void free_all(pimc_t h)
 {
     void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar,
                     h->ticket, h->red, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
-                    h->dense, h->small, h->y64, h->I64};
+                    h->dense, h->small, h->y64, h->I64, h->trace, h->hmc.hs, h->hmc.Q, h->hmc.P,
+                    h->hmc.g, h->hmc.invm};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    if (h->hmc_exec) cudaGraphExecDestroy(h->hmc_exec);
 }
 
 // clear statistics, counters and windows (sweep counter and beta follow the schedule)
@@ -331,6 +343,7 @@ const char* pimc_last_error(pimc_t h) { return h ? h->err.c_str() : g_create_err
 int pimc_set_stream(pimc_t h, void* stream)
 {
     if (!h) return PIMC_ERR_ARG;
+    h->ctx_version++;
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->own_stream) cudaStreamDestroy(h->stream);
     h->own_stream = false;
@@ -344,6 +357,7 @@ int pimc_set_precision(pimc_t h, int precision)
     if (precision != PIMC_FP64 && precision != PIMC_FP32_MIXED)
         return fail(h, PIMC_ERR_ARG, "unknown precision %d", precision);
     if (precision == h->prec) return PIMC_OK;
+    h->ctx_version++;
     const int64_t nd = (int64_t)h->D * (h->M + 1);
     std::vector<double> X(nd), S(nd);
     int r = get_rows(h, X.data(), h->X, h->ldx, h->M + 1);
@@ -450,6 +464,7 @@ int pimc_set_steps(pimc_t h, const double* sigma_x, int per_site, const double* 
 int pimc_set_schedule(pimc_t h, int64_t n_init, int64_t n_skip, double beta0, int64_t n_cool, double f_acc, double alpha)
 {
     if (!h) return PIMC_ERR_ARG;
+    h->ctx_version++;
     if (n_skip < 1 || n_init < 0 || n_cool < 0 || !(beta0 > 0.0) || beta0 > 1.0 || !std::isfinite(f_acc) ||
         !std::isfinite(alpha))
         return fail(h, PIMC_ERR_ARG, "bad schedule");
@@ -470,6 +485,7 @@ int pimc_set_schedule(pimc_t h, int64_t n_init, int64_t n_skip, double beta0, in
 int pimc_set_chain(pimc_t h, uint32_t chain)
 {
     if (!h) return PIMC_ERR_ARG;
+    h->ctx_version++;
     h->chain = chain;
     return PIMC_OK;
 }
@@ -600,6 +616,7 @@ int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples)
 int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const double* lo, const double* hi, int n_bins)
 {
     if (!h) return PIMC_ERR_ARG;
+    h->ctx_version++;
     if (n_sel < 1 || n_sel > kMaxSel || n_bins < 1 || n_bins > kMaxBins || !comp_index || !lo || !hi)
         return fail(h, PIMC_ERR_ARG, "bad histogram configuration");
     const int64_t nc = (int64_t)h->D * (h->M + 1) + h->NP;
@@ -631,6 +648,119 @@ int pimc_histograms(pimc_t h, uint64_t* counts)
     if (!counts) return fail(h, PIMC_ERR_ARG, "counts is NULL");
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaMemcpy(counts, h->hist, sizeof(uint64_t) * h->n_sel * (h->n_bins + 2), cudaMemcpyDeviceToHost));
+    return PIMC_OK;
+}
+
+int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv_mass, uint64_t seed,
+             int64_t* n_accepted)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_hmc before data/params");
+    if (n_traj < 0 || n_leap < 1 || n_leap > 100000 || !(eps > 0.0) || !std::isfinite(eps))
+        return fail(h, PIMC_ERR_ARG, "bad HMC arguments (n_traj >= 0, 1 <= n_leap, eps > 0)");
+    const int64_t nq = (int64_t)h->D * (h->M + 1) + h->NP;
+    if (!h->hmc.hs) {
+        CK(h, cudaMalloc(&h->hmc.hs, sizeof(HmcScalars)));
+        CK(h, cudaMalloc(&h->hmc.Q, sizeof(double) * nq));
+        CK(h, cudaMalloc(&h->hmc.P, sizeof(double) * nq));
+        CK(h, cudaMalloc(&h->hmc.g, sizeof(double) * nq));
+        CK(h, cudaMalloc(&h->hmc.invm, sizeof(double) * nq));
+        CK(h, cudaMemset(h->hmc.hs, 0, sizeof(HmcScalars)));
+    }
+    {
+        std::vector<double> im((size_t)nq, 1.0);
+        if (inv_mass) {
+            for (int64_t j = 0; j < nq; ++j) {
+                if (!(inv_mass[j] >= 0.0) || !std::isfinite(inv_mass[j]))
+                    return fail(h, PIMC_ERR_ARG, "inv_mass must be finite and >= 0");
+                im[j] = inv_mass[j];
+            }
+        }
+        CK(h, cudaMemcpyAsync(h->hmc.invm, im.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    unsigned long long acc0 = 0;
+    if (n_accepted) {
+        HmcScalars hs;
+        CK(h, cudaMemcpy(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost));
+        acc0 = hs.n_acc;
+    }
+    // one trajectory = a fixed launch sequence: capture it once as a CUDA graph
+    // (re-captured when n_leap, eps, seed or the precision change)
+    if (!h->hmc_exec || h->hmc_leap != n_leap || h->hmc_eps != eps || h->hmc_seed != seed || h->hmc_prec != h->prec ||
+        h->hmc_version != h->ctx_version) {
+        if (h->hmc_exec) {
+            cudaGraphExecDestroy(h->hmc_exec);
+            h->hmc_exec = nullptr;
+        }
+        if (h->stream) {
+            cudaGraph_t graph = nullptr;
+            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = launch_hmc_trajectory(h->model, h->prec, make_ctx(h), h->hmc, n_leap, eps, seed, h->stream);
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->hmc_exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            CK(h, e);
+        }
+        h->hmc_leap = n_leap;
+        h->hmc_eps = eps;
+        h->hmc_seed = seed;
+        h->hmc_prec = h->prec;
+        h->hmc_version = h->ctx_version;
+    }
+    for (int64_t t = 0; t < n_traj; ++t) {
+        if (h->hmc_exec) CK(h, cudaGraphLaunch(h->hmc_exec, h->stream));
+        else CK(h, launch_hmc_trajectory(h->model, h->prec, make_ctx(h), h->hmc, n_leap, eps, seed, h->stream));
+    }
+    if (n_accepted) {
+        HmcScalars hs;
+        CK(h, cudaMemcpyAsync(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        *n_accepted = (int64_t)(hs.n_acc - acc0);
+    }
+    return PIMC_OK;
+}
+
+int pimc_set_param_trace(pimc_t h, int64_t cap)
+{
+    if (!h) return PIMC_ERR_ARG;
+    h->ctx_version++;
+    if (cap < 0 || cap > ((int64_t)1 << 28)) return fail(h, PIMC_ERR_ARG, "trace capacity must be in [0, 2^28]");
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->trace) {
+        CK(h, cudaFree(h->trace));
+        h->trace = nullptr;
+    }
+    h->trace_cap = 0;
+    if (cap > 0) {
+        CK(h, cudaMalloc(&h->trace, sizeof(double) * (size_t)cap * h->NP));
+        h->trace_cap = cap;
+    }
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    h->hs.tr_n = 0;
+    return push_state(h);
+}
+
+int pimc_param_trace(pimc_t h, double* out, int64_t cap, int64_t* n_written)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->trace) return fail(h, PIMC_ERR_STATE, "no parameter trace configured");
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    const int64_t total = h->hs.tr_n;
+    int64_t k = std::min<int64_t>(total, h->trace_cap);
+    if (out) k = std::min<int64_t>(k, cap);
+    if (n_written) *n_written = k;
+    if (!out || k == 0) return PIMC_OK;
+    // the last k entries in chronological order: ring slots (total-k .. total-1) mod cap
+    std::vector<double> ring((size_t)h->trace_cap * h->NP);
+    CK(h, cudaMemcpy(ring.data(), h->trace, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < k; ++i) {
+        const int64_t slot = (total - k + i) % h->trace_cap;
+        memcpy(out + i * h->NP, &ring[(size_t)slot * h->NP], sizeof(double) * h->NP);
+    }
     return PIMC_OK;
 }
 
@@ -702,7 +832,7 @@ int pimc_launch_info(pimc_t h, int* grid, int* block)
 {
     if (!h) return PIMC_ERR_ARG;
     if (grid) *grid = h->grid;
-    if (block) *block = kBlock;
+    if (block) *block = kSweepBlock;
     return PIMC_OK;
 }
 
@@ -722,6 +852,7 @@ int pimc_debug_skip_arrive(pimc_t h, int cta)
 
 int pimc_set_grid(pimc_t h, int grid)
 {
+    if (h) h->ctx_version++;
     if (!h || grid < 0) return h ? fail(h, PIMC_ERR_ARG, "grid must be >= 0") : PIMC_ERR_ARG;
     h->grid_override = grid;
     choose_grid(h);
@@ -917,6 +1048,7 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
     hs.status = 0;
     hs.abort = 0;
     h->hs = hs;
+    h->ctx_version++;
     CK(h, cudaMemset(h->bar, 0, sizeof(unsigned) * 4));
     choose_grid(h);
     return push_state(h);

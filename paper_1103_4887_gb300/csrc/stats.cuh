@@ -1,0 +1,59 @@
+// Path statistics (Sec. 4.1): running shifted sums S1 += x - r, S2 += (x - r)^2
+// in FP64 (r = first recorded value) and equal-width bin counts with
+// under/overflow slots, for the sites [n0, n1) a caller owns and, when
+// `params_here`, the parameters.  Shared by the sweep and HMC kernels.
+#pragma once
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace pimc {
+
+__device__ __forceinline__ int64_t hist_slot(double v, double lo, double hi, int nb)
+{
+    if (!(v >= lo)) return 0;
+    if (v >= hi) return nb + 1;
+    const double t = (v - lo) / (hi - lo);
+    int64_t b = (int64_t)floor(t * (double)nb);
+    if (b > nb - 1) b = nb - 1;
+    return 1 + b;
+}
+
+__device__ __forceinline__ void accumulate(const Ctx& c, int64_t ci, double v, bool first_rec)
+{
+    if (first_rec) c.shift[ci] = v;
+    const double d = v - c.shift[ci];
+    c.S1[ci] += d;
+    c.S2[ci] += d * d;
+}
+
+// Thread t of nt records its share; p is the current parameter vector.
+template <class Model, class R>
+__device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_here, const double* p,
+                              bool first_rec, int t, int nt)
+{
+    constexpr int D = Model::D, NP = Model::NP;
+    const int64_t M = c.M, nx = (int64_t)D * (M + 1);
+    const R* X = (const R*)c.X;
+    for (int64_t n = n0 + t; n < n1; n += nt) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) accumulate(c, (int64_t)a * (M + 1) + n, (double)X[a * c.ldx + n], first_rec);
+    }
+    if (params_here && t < NP) accumulate(c, nx + t, p[t], first_rec);
+    for (int kk = t; kk < c.n_sel; kk += nt) {
+        const int64_t ci = c.h_comp[kk];
+        double v;
+        bool mine;
+        if (ci < nx) {
+            const int64_t a = ci / (M + 1), n = ci - a * (M + 1);
+            mine = (n >= n0 && n < n1);
+            v = mine ? (double)X[a * c.ldx + n] : 0.0;
+        } else {
+            mine = params_here;
+            v = p[ci - nx];
+        }
+        if (mine) c.hist[(int64_t)kk * (c.n_bins + 2) + hist_slot(v, c.h_lo[kk], c.h_hi[kk], c.n_bins)] += 1ull;
+    }
+}
+
+}  // namespace pimc

@@ -11,21 +11,38 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "stats.cuh"
 
 namespace pimc {
 
-struct SweepShared {
+// Scalar constants of the action in the arithmetic type, formed once per
+// kernel so the per-site code does no FP64 -> FP32 conversions.
+template <class R> struct Coef {
+    R dt, Rm, Rf[kMaxD];
+    __device__ __forceinline__ explicit Coef(const Ctx& c)
+    {
+        dt = R(c.dt);
+        Rm = R(c.Rm);
+#pragma unroll
+        for (int a = 0; a < kMaxD; ++a) Rf[a] = R(c.Rf[a]);
+    }
+};
+
+template <class R> struct SweepShared {
     double p[kMaxP], lo[kMaxP], hi[kMaxP], sigp[kMaxP];
     double beta;
     long long sweep, J;
     unsigned fidx, free_mask, nred;
     unsigned accp_win[kMaxP];
     unsigned long long par_acc[kMaxP], par_prop[kMaxP];
-    double pnew, uacc;
-    double pq[kMaxP];
-    int inbox, abort;
-    double wsum[kBlock / 32];
+    double pnew[kMaxP], elog[kMaxP];  // this sweep's proposal and -log u per parameter
+    int inbox[kMaxP];
+    R q_cur[kMaxP];                   // current model parameters in R
+    R q_new[kMaxP][kMaxP];            // proposed vector for each parameter move, in R
+    R tpart[kSweepBlock];           // per-thread partial sums of a parameter move
+    int abort;
     unsigned long long site_acc[2], site_prop[2], nonfinite;
+    long long tr_n;
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -35,39 +52,36 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Grid-wide barrier (generation counter).  The wait is bounded by c.wait_ns;
-// on expiry the CTA flags kStatusTimeout and the abort word, and every CTA
-// leaves the launch at its next barrier.  Returns false when leaving.
+// Grid-wide barrier on one 32-bit word: every CTA adds 1, except CTA 0 which
+// adds 2^31 - (G - 1), so the word's top bit flips exactly when all G CTAs
+// have arrived and its low bits return to their old value.  Each CTA waits for
+// the flip relative to the value its own add returned (a fence before the add
+// publishes the CTA's writes; a fence after the wait orders its later reads).
+// The wait is bounded by c.wait_ns: on expiry the CTA flags kStatusTimeout and
+// the abort word, and every CTA leaves the launch at its next barrier.
+// Returns false when leaving.
 __device__ bool grid_barrier(const Ctx& c, int* s_abort)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(c.bar[0]);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gen(c.bar[1]);
-        cuda::atomic_ref<int, cuda::thread_scope_device> abrt(c.st->abort);
         int ok = 1;
-        const unsigned g = gen.load(cuda::memory_order_acquire);
+        const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
         __threadfence();
-        if ((int)blockIdx.x != c.skip_cta) {
-            const unsigned prev = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-            if (prev == gridDim.x - 1) {
-                cnt.store(0u, cuda::memory_order_relaxed);
-                gen.store(g + 1u, cuda::memory_order_release);
-            }
-        }
-        if (gen.load(cuda::memory_order_acquire) == g) {
-            const unsigned long long t0 = global_ns();
-            unsigned ns = 32;
-            while (gen.load(cuda::memory_order_acquire) == g) {
-                if (abrt.load(cuda::memory_order_relaxed)) { ok = 0; break; }
+        unsigned old = 0u;
+        if ((int)blockIdx.x != c.skip_cta) old = atomicAdd(&c.bar[0], add);
+        else old = *(volatile unsigned*)&c.bar[0];
+        unsigned spins = 0;
+        const unsigned long long t0 = global_ns();
+        while (((old ^ *(volatile unsigned*)&c.bar[0]) & 0x80000000u) == 0u) {
+            if ((++spins & 63u) == 0u) {
+                if (*(volatile int*)&c.st->abort) { ok = 0; break; }
                 if ((long long)(global_ns() - t0) > c.wait_ns) {
                     atomicOr(&c.st->status, kStatusTimeout);
-                    abrt.store(1, cuda::memory_order_relaxed);
+                    atomicExch(&c.st->abort, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(ns);
-                if (ns < 512) ns <<= 1;
+                if (spins > 4096u) __nanosleep(64);
             }
         }
         __threadfence();
@@ -80,33 +94,47 @@ __device__ bool grid_barrier(const Ctx& c, int* s_abort)
 // Local change of action for x_n -> xp (Fig. 1 steps (c)-(g)): the
 // measurement term at n (n >= 1), the model-error term eps_n against the
 // cached f(x_{n-1}) (n >= 1) and eps_{n+1} against f(xp) (n <= M-1).
+// Nb holds the neighbourhood values loaded before the map is evaluated.
+template <class R, int D> struct Nbhd {
+    R yn, fprev[D], xn1[D], fcur[D];
+};
+
 template <class Model, class R>
-__device__ __forceinline__ R site_delta(const Ctx& c, int64_t n, const R* x, const R* xp, const R* fp,
-                                        R beta, const R* Fc)
+__device__ __forceinline__ void load_nbhd(const Ctx& c, int64_t n, const R* Fc, Nbhd<R, Model::D>& nb)
 {
     constexpr int D = Model::D;
     const R* X = (const R*)c.X;
-    const R* y = (const R*)c.y;
-    R dA = R(0);
     if (n >= 1) {
-        const R yn = y[n];
-        dA += sqdiff<R>(R(c.Rm), xp[0] - yn, x[0] - yn);
-        R dAf = R(0);
+        nb.yn = ((const R*)c.y)[n];
+#pragma unroll
+        for (int a = 0; a < D; ++a) nb.fprev[a] = Fc[a * c.ldf + n - 1];
+    }
+    if (n < c.M) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const R fprev = Fc[a * c.ldf + n - 1];
-            dAf += sqdiff<R>(R(c.Rf[a]), xp[a] - fprev, x[a] - fprev);
+            nb.xn1[a] = X[a * c.ldx + n + 1];
+            nb.fcur[a] = Fc[a * c.ldf + n];
         }
+    }
+}
+
+template <class Model, class R>
+__device__ __forceinline__ R site_delta(const Ctx& c, const Coef<R>& k, int64_t n, const R* x, const R* xp,
+                                        const R* fp, R beta, const Nbhd<R, Model::D>& nb)
+{
+    constexpr int D = Model::D;
+    R dA = R(0);
+    if (n >= 1) {
+        dA += sqdiff<R>(k.Rm, xp[0] - nb.yn, x[0] - nb.yn);
+        R dAf = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) dAf += sqdiff<R>(k.Rf[a], xp[a] - nb.fprev[a], x[a] - nb.fprev[a]);
         dA += beta * dAf;
     }
     if (n < c.M) {
         R dAf = R(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const R xn1 = X[a * c.ldx + n + 1];
-            const R fc = Fc[a * c.ldf + n];
-            dAf += sqdiff<R>(R(c.Rf[a]), xn1 - fp[a], xn1 - fc);
-        }
+        for (int a = 0; a < D; ++a) dAf += sqdiff<R>(k.Rf[a], nb.xn1[a] - fp[a], nb.xn1[a] - nb.fcur[a]);
         dA += beta * dAf;
     }
     return dA;
@@ -129,25 +157,29 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
     u = Num<R>::uni(w.x, w.y);
 }
 
-// One site move: proposal, f(x'), Delta A_n, Metropolis, store on accept.
+// One site move: proposal, f(x'), Delta A_n, Metropolis (as dA < -log u,
+// Eq. (Paccept)), store on accept.
 template <class Model, class R>
-__device__ __forceinline__ bool site_move(const Ctx& c, int64_t n, long long s, const R* pr, R beta,
-                                          R* Fc, unsigned long long& nonfinite)
+__device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
+                                          R beta, R* Fc, unsigned long long& nonfinite)
 {
     constexpr int D = Model::D;
     R* X = (R*)c.X;
     const R* sig = (const R*)c.sig;
     R x[D], xp[D], fp[D], z[D], u;
+    Nbhd<R, D> nb;
 #pragma unroll
     for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    load_nbhd<Model, R>(c, n, Fc, nb);
     site_draws<Model, R>(c, s, n, z, u);
+    const R E = neglog<R>(u);
 #pragma unroll
     for (int a = 0; a < D; ++a) xp[a] = x[a] + sig[a * c.ldx + n] * z[a];
     const bool has_next = n < c.M;
-    if (has_next) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], R(c.dt), fp);
-    const R dA = site_delta<Model, R>(c, n, x, xp, fp, beta, Fc);
+    if (has_next) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], k.dt, fp);
+    const R dA = site_delta<Model, R>(c, k, n, x, xp, fp, beta, nb);
     if (!isfinite(dA)) ++nonfinite;
-    const bool acc = metropolis<R>(dA, u);
+    const bool acc = dA < E;
     if (acc) {
 #pragma unroll
         for (int a = 0; a < D; ++a) X[a * c.ldx + n] = xp[a];
@@ -163,20 +195,24 @@ __device__ __forceinline__ bool site_move(const Ctx& c, int64_t n, long long s, 
 // Site n's share of a parameter move: f(x_n, p') into the inactive cache and
 // beta/2 sum_a Rf_a [(x_{n+1} - f')^2 - (x_{n+1} - f)^2].
 template <class Model, class R>
-__device__ __forceinline__ R param_term(const Ctx& c, int64_t n, const R* pq, R beta, const R* Fc, R* Fn)
+__device__ __forceinline__ R param_term(const Ctx& c, const Coef<R>& k, int64_t n, const R* pq, R beta,
+                                        const R* Fc, R* Fn)
 {
     constexpr int D = Model::D;
     const R* X = (const R*)c.X;
-    R x[D], fp[D];
+    R x[D], fp[D], xn1[D], fc[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
-    rk4_map<Model, R>(x, pq, ((const R*)c.I)[n], R(c.dt), fp);
+    for (int a = 0; a < D; ++a) {
+        x[a] = X[a * c.ldx + n];
+        xn1[a] = X[a * c.ldx + n + 1];
+        fc[a] = Fc[a * c.ldf + n];
+    }
+    rk4_map<Model, R>(x, pq, ((const R*)c.I)[n], k.dt, fp);
     R t = R(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         Fn[a * c.ldf + n] = fp[a];
-        const R xn1 = X[a * c.ldx + n + 1];
-        t += beta * sqdiff<R>(R(c.Rf[a]), xn1 - fp[a], xn1 - Fc[a * c.ldf + n]);
+        t += beta * sqdiff<R>(k.Rf[a], xn1[a] - fp[a], xn1[a] - fc[a]);
     }
     return t;
 }
@@ -188,7 +224,8 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Fixed-order CTA sum; result valid in thread 0.
+// Fixed-order CTA sum of NT threads; result valid in thread 0.
+template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* wsum)
 {
     v = warp_sum(v);
@@ -198,26 +235,17 @@ __device__ __forceinline__ double block_sum(double v, double* wsum)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int k = 0; k < kBlock / 32; ++k) t += wsum[k];
+        for (int k = 0; k < NT / 32; ++k) t += wsum[k];
     return t;
 }
 
-__device__ __forceinline__ int64_t hist_slot(double v, double lo, double hi, int nb)
-{
-    if (!(v >= lo)) return 0;
-    if (v >= hi) return nb + 1;
-    const double t = (v - lo) / (hi - lo);
-    int64_t b = (int64_t)floor(t * (double)nb);
-    if (b > nb - 1) b = nb - 1;
-    return 1 + b;
-}
-
 template <class Model, class R>
-__global__ void __launch_bounds__(kBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
+__global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
 {
-    constexpr int D = Model::D, NP = Model::NP;
-    __shared__ SweepShared sh;
+    constexpr int D = Model::D, NP = Model::NP, NT = kSweepBlock;
+    __shared__ SweepShared<R> sh;
     const int tid = threadIdx.x;
+    const Coef<R> kc(c);
     if (tid == 0) {
         const DevState* g = c.st;
         for (int l = 0; l < kMaxP; ++l) {
@@ -225,31 +253,54 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
             sh.accp_win[l] = g->accp_win[l]; sh.par_acc[l] = g->par_acc[l]; sh.par_prop[l] = g->par_prop[l];
         }
         sh.beta = g->beta; sh.sweep = g->sweep; sh.J = g->J; sh.fidx = g->fidx;
-        sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0;
+        sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0; sh.tr_n = g->tr_n;
         sh.site_acc[0] = sh.site_acc[1] = sh.site_prop[0] = sh.site_prop[1] = sh.nonfinite = 0ull;
+        Model::prep(sh.p, sh.q_cur);
     }
     __syncthreads();
 
     const int64_t M = c.M;
     const int64_t n0 = (int64_t)blockIdx.x * c.tile;
     const int64_t n1 = min(n0 + c.tile, M + 1);
-    const int64_t nx = (int64_t)D * (M + 1);
     unsigned long long my_acc[2] = {0ull, 0ull}, my_prop[2] = {0ull, 0ull}, my_nf = 0ull;
     R* X = (R*)c.X;
     R* sig = (R*)c.sig;
 
     for (int64_t k = 0; k < n_sweeps; ++k) {
         const long long s = sh.sweep;
+        // This sweep's parameter proposals, one lane per parameter of the last
+        // warp (idle in the site phases at small M).  p_l changes only in its
+        // own move, so p'_l = p_l + sigma_l z_l is fixed at the sweep's start;
+        // the proposed vector for move l is completed after the earlier moves.
+        if (tid >= NT - 32 && tid - (NT - 32) < NP) {
+            const int l = tid - (NT - 32);
+            if ((sh.free_mask >> l) & 1u) {
+                double z0, z1;
+                Num<double>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u), z0, z1);
+                const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
+                const double pl = sh.p[l] + sh.sigp[l] * z0;
+                sh.pnew[l] = pl;
+                sh.elog[l] = -log(u01d(w.x, w.y));
+                sh.inbox[l] = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
+                double pv[kMaxP];
+                for (int q = 0; q < kMaxP; ++q) pv[q] = sh.p[q];
+                pv[l] = pl;
+                Model::prep(pv, sh.q_new[l]);
+            }
+        }
+        // (no barrier here: the draws overlap the even site phase and are
+        // published by the barrier that ends it)
         const R beta = R(sh.beta);
         R pr[kMaxP];
-        Model::prep(sh.p, pr);
+#pragma unroll
+        for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
 
         // ---- even then odd sites (Sec. 4.1) ----
         for (int parity = 0; parity < 2; ++parity) {
             R* Fc = (R*)c.F[sh.fidx];
             const int64_t first = n0 + (((n0 & 1) != parity) ? 1 : 0);
-            for (int64_t n = first + 2 * (int64_t)tid; n < n1; n += 2 * kBlock) {
-                my_acc[parity] += site_move<Model, R>(c, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
+            for (int64_t n = first + 2 * (int64_t)tid; n < n1; n += 2 * NT) {
+                my_acc[parity] += site_move<Model, R>(c, kc, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
                 my_prop[parity] += 1ull;
             }
             if (!grid_barrier(c, &sh.abort)) goto done;
@@ -258,94 +309,62 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
         // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
         for (int l = 0; l < NP; ++l) {
             if (!((sh.free_mask >> l) & 1u)) continue;
-            if (tid == 0) {
-                double z0, z1;
-                Num<double>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u), z0, z1);
-                const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
-                const double pl = sh.p[l] + sh.sigp[l] * z0;
-                sh.pnew = pl;
-                for (int q = 0; q < kMaxP; ++q) sh.pq[q] = sh.p[q];
-                sh.pq[l] = pl;
-                sh.uacc = u01d(w.x, w.y);
-                sh.inbox = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
-                sh.par_prop[l] += 1ull;
-            }
+            if (tid == 0) sh.par_prop[l] += 1ull;
+            if (!sh.inbox[l]) continue;  // out of the prior box: rejected without compute
+            R pq[kMaxP];
+#pragma unroll
+            for (int q = 0; q < kMaxP; ++q) pq[q] = (q == l || (q == 7 && l == 6)) ? sh.q_new[l][q] : pr[q];
+            const R* Fc = (const R*)c.F[sh.fidx];
+            R* Fn = (R*)c.F[sh.fidx ^ 1u];
+            R part = R(0);
+            const int64_t nend = min(n1, M);
+            for (int64_t n = n0 + tid; n < nend; n += NT) part += param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn);
+            // CTA sum in FP64 from the per-thread partials up, by one warp (pairwise within a lane)
+            sh.tpart[tid] = part;
             __syncthreads();
-            if (sh.inbox) {
-                R pq[kMaxP];
-                Model::prep(sh.pq, pq);
-                const R* Fc = (const R*)c.F[sh.fidx];
-                R* Fn = (R*)c.F[sh.fidx ^ 1u];
-                R part = R(0);
-                const int64_t nend = min(n1, M);
-                for (int64_t n = n0 + tid; n < nend; n += kBlock)
-                    part += param_term<Model, R>(c, n, pq, beta, Fc, Fn);
-                const double bs = block_sum((double)part, sh.wsum);
-                const unsigned slot = sh.nred & 1u;
-                if (tid == 0) c.partials[slot * kMaxGrid + blockIdx.x] = bs;
-                if (!grid_barrier(c, &sh.abort)) goto done;
-                if (tid < 32) {
-                    double v = 0.0;
-                    for (int i = tid; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
-                    v = warp_sum(v);
-                    if (tid == 0) {
-                        if (metropolis<double>(v, sh.uacc)) {
-                            sh.p[l] = sh.pnew;
-                            sh.fidx ^= 1u;
-                            sh.accp_win[l] += 1u;
-                            sh.par_acc[l] += 1ull;
-                        }
-                        sh.nred += 1u;
+            const unsigned slot = sh.nred & 1u;
+            if (tid < 32) {
+                double t[NT / 32];
+#pragma unroll
+                for (int q = 0; q < NT / 32; ++q) t[q] = (double)sh.tpart[tid + 32 * q];
+#pragma unroll
+                for (int w = NT / 64; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w; ++q) t[q] += t[q + w];
+                const double v = warp_sum(t[0]);
+                if (tid == 0) c.partials[slot * kMaxGrid + blockIdx.x] = v;
+            }
+            if (!grid_barrier(c, &sh.abort)) goto done;
+            if (tid < 32) {
+                double v = 0.0;
+                for (int i = tid; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
+                v = warp_sum(v);
+                if (tid == 0) {
+                    // Eq. (Paccept) as dA < -log u (NaN compares false)
+                    if (v < sh.elog[l]) {
+                        sh.p[l] = sh.pnew[l];
+                        sh.q_cur[l] = sh.q_new[l][l];
+                        if (l == 6) sh.q_cur[7] = sh.q_new[l][7];
+                        sh.fidx ^= 1u;
+                        sh.accp_win[l] += 1u;
+                        sh.par_acc[l] += 1ull;
                     }
+                    sh.nred += 1u;
                 }
-                __syncthreads();
-                Model::prep(sh.p, pr);
             }
             __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
         }
+        __syncthreads();
 
         // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
         const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
-        if (record) {
-            const bool first_rec = (sh.J == 0);
-            for (int64_t n = n0 + tid; n < n1; n += kBlock) {
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const double v = (double)X[a * c.ldx + n];
-                    const int64_t ci = (int64_t)a * (M + 1) + n;
-                    if (first_rec) c.shift[ci] = v;
-                    const double d = v - c.shift[ci];
-                    c.S1[ci] += d;
-                    c.S2[ci] += d * d;
-                }
-            }
-            if (blockIdx.x == 0 && tid < NP) {
-                const double v = sh.p[tid];
-                const int64_t ci = nx + tid;
-                if (first_rec) c.shift[ci] = v;
-                const double d = v - c.shift[ci];
-                c.S1[ci] += d;
-                c.S2[ci] += d * d;
-            }
-            for (int kk = tid; kk < c.n_sel; kk += kBlock) {
-                const int64_t ci = c.h_comp[kk];
-                double v;
-                bool mine;
-                if (ci < nx) {
-                    const int64_t a = ci / (M + 1), n = ci - a * (M + 1);
-                    mine = (n >= n0 && n < n1);
-                    v = mine ? (double)X[a * c.ldx + n] : 0.0;
-                } else {
-                    mine = (blockIdx.x == 0);
-                    v = sh.p[ci - nx];
-                }
-                if (mine) c.hist[(int64_t)kk * (c.n_bins + 2) + hist_slot(v, c.h_lo[kk], c.h_hi[kk], c.n_bins)] += 1ull;
-            }
-        }
+        if (record) record_sample<Model, R>(c, n0, n1, blockIdx.x == 0, sh.p, sh.J == 0, tid, NT);
 
         // ---- step-size adaptation during burn-in (Sec. 4.2) ----
         if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
-            for (int64_t n = n0 + tid; n < n1; n += kBlock) {
+            for (int64_t n = n0 + tid; n < n1; n += NT) {
                 const double fac = 1.0 + c.alpha * ((double)c.acc_win[n] / (double)c.n_skip - c.f_acc);
 #pragma unroll
                 for (int a = 0; a < D; ++a) sig[a * c.ldx + n] = R((double)sig[a * c.ldx + n] * fac);
@@ -360,12 +379,17 @@ __global__ void __launch_bounds__(kBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
             }
         }
 
+        // ---- parameter trace (for effective-sample-size diagnostics) ----
+        if (c.trace && blockIdx.x == 0 && tid < NP)
+            c.trace[(sh.tr_n % c.trace_cap) * NP + tid] = sh.p[tid];
+
         // ---- annealing, Eq. (fbeta): beta_{s+1} = beta_s f_beta until N_cool ----
         __syncthreads();
         if (tid == 0) {
             sh.beta = (s + 1 < c.n_cool) ? sh.beta * c.fbeta : 1.0;
             sh.sweep = s + 1;
             if (record) sh.J += 1;
+            if (c.trace) sh.tr_n += 1;
         }
         __syncthreads();
     }
@@ -390,7 +414,7 @@ done:
                 g->p[l] = sh.p[l]; g->sigp[l] = sh.sigp[l]; g->accp_win[l] = sh.accp_win[l];
                 g->par_acc[l] = sh.par_acc[l]; g->par_prop[l] = sh.par_prop[l];
             }
-            g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx;
+            g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx; g->tr_n = sh.tr_n;
         }
     }
 }
@@ -401,14 +425,14 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, cuda
     Ctx cc = c;
     int64_t ns = n_sweeps;
     void* args[] = {(void*)&cc, (void*)&ns};
-    return cudaLaunchCooperativeKernel((const void*)sweep_kernel<Model, R>, dim3(grid), dim3(kBlock), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)sweep_kernel<Model, R>, dim3(grid), dim3(kSweepBlock), args, 0, s);
 }
 
 template <class Model, class R>
 static int max_grid_t(int device)
 {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Model, R>, kBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Model, R>, kSweepBlock, 0) != cudaSuccess)
         return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     return per_sm * sms;
@@ -448,15 +472,18 @@ __global__ void __launch_bounds__(kBlock) site_delta_kernel(Ctx c, const double*
     if (n > c.M) return;
     const R* X = (const R*)c.X;
     const R* Fc = (const R*)c.F[c.st->fidx];
+    const Coef<R> kc(c);
     R pr[kMaxP];
     Model::prep(c.st->p, pr);
     R x[D], xp[D], fp[D];
+    Nbhd<R, D> nb;
     for (int a = 0; a < D; ++a) {
         x[a] = X[a * c.ldx + n];
         xp[a] = R(Xp[a * (c.M + 1) + n]);
     }
-    if (n < c.M) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], R(c.dt), fp);
-    dA[n] = (double)site_delta<Model, R>(c, n, x, xp, fp, R(beta), Fc);
+    load_nbhd<Model, R>(c, n, Fc, nb);
+    if (n < c.M) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], kc.dt, fp);
+    dA[n] = (double)site_delta<Model, R>(c, kc, n, x, xp, fp, R(beta), nb);
 }
 
 // Full-path parameter change of action: per-CTA sums in FP64, then the last
@@ -473,10 +500,11 @@ __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, doubl
     pd[l] = pl_new;
     R pq[kMaxP];
     Model::prep(pd, pq);
+    const Coef<R> kc(c);
     R part = R(0);
     for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < c.M; n += (int64_t)gridDim.x * kBlock)
-        part += param_term<Model, R>(c, n, pq, R(beta), Fc, Fn);
-    const double bs = block_sum((double)part, wsum);
+        part += param_term<Model, R>(c, kc, n, pq, R(beta), Fc, Fn);
+    const double bs = block_sum<kBlock>((double)part, wsum);
     if (threadIdx.x == 0) {
         c.red[blockIdx.x] = bs;
         __threadfence();

@@ -28,9 +28,9 @@ _ERRNAMES = {ERR_ARG: "PIMC_ERR_ARG", ERR_STATE: "PIMC_ERR_STATE", ERR_CUDA: "PI
 EXPORTS = [
     "pimc_create", "pimc_destroy", "pimc_last_error", "pimc_set_stream", "pimc_set_precision",
     "pimc_set_data", "pimc_load_data", "pimc_set_params", "pimc_set_path", "pimc_set_steps", "pimc_set_schedule",
-    "pimc_set_chain", "pimc_sweep", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
+    "pimc_set_chain", "pimc_sweep", "pimc_hmc", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
-    "pimc_histograms", "pimc_histogram_shape", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
+    "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
     "pimc_debug_skip_arrive", "pimc_set_grid", "pimc_action_static",
 ]
@@ -83,6 +83,7 @@ def _declare(L):
         "pimc_set_chain": [_vp, ctypes.c_uint32],
         "pimc_sweep": [_vp, _i64, ctypes.c_uint64],
         "pimc_sync": [_vp],
+        "pimc_hmc": [_vp, _i64, _int, _d, _vp, ctypes.c_uint64, _vp],
         "pimc_action": [_vp, _vp, _vp, _vp],
         "pimc_grad": [_vp, _d, _vp, _vp],
         "pimc_action_dev": [_vp, _vp, _vp, _vp, _vp],
@@ -93,6 +94,8 @@ def _declare(L):
         "pimc_set_histograms": [_vp, _int, _vp, _vp, _vp, _int],
         "pimc_histograms": [_vp, _vp],
         "pimc_histogram_shape": [_vp, _vp, _vp],
+        "pimc_set_param_trace": [_vp, _i64],
+        "pimc_param_trace": [_vp, _vp, _i64, _vp],
         "pimc_get_state": [_vp, _vp, _vp],
         "pimc_get_steps": [_vp, _vp, _vp],
         "pimc_get_sweep": [_vp, _vp, _vp],
@@ -221,6 +224,15 @@ class Sampler:
         if sync:
             self.sync()
 
+    def hmc(self, n_traj, n_leap, eps, inv_mass=None, seed=0):
+        """Whole-path HMC trajectories; returns the number accepted."""
+        im = None if inv_mass is None else _f64(inv_mass)
+        if im is not None:
+            assert im.size == self.D * (self.M + 1) + self.Np
+        n = np.zeros(1, dtype=np.int64)
+        self._ck(self._L.pimc_hmc(self._h, int(n_traj), int(n_leap), float(eps), _p(im), int(seed), _p(n)))
+        return int(n[0])
+
     def sync(self):
         self._ck(self._L.pimc_sync(self._h))
 
@@ -272,6 +284,16 @@ class Sampler:
         out = np.zeros(ns.value * (nb.value + 2), dtype=np.uint64)
         self._ck(self._L.pimc_histograms(self._h, _p(out)))
         return out.reshape(ns.value, nb.value + 2)
+
+    def set_param_trace(self, cap):
+        self._ck(self._L.pimc_set_param_trace(self._h, int(cap)))
+
+    def param_trace(self):
+        n = np.zeros(1, dtype=np.int64)
+        self._ck(self._L.pimc_param_trace(self._h, None, 0, _p(n)))
+        out = np.zeros(int(n[0]) * self.Np)
+        self._ck(self._L.pimc_param_trace(self._h, _p(out), int(n[0]), _p(n)))
+        return out.reshape(int(n[0]), self.Np)
 
     def state(self):
         X = np.zeros(self.D * (self.M + 1))

@@ -1,0 +1,94 @@
+"""Whole-path HMC on the GPU (pimc_hmc) against the oracle's HMC and against
+the closed-form linear-Gaussian posterior.
+
+* replay: same seed and Philox counters, trajectory by trajectory from the same
+  state; accept decisions must agree (a differing decision must sit within
+  1e-9 of its threshold) and accepted end points must agree to the leapfrog's
+  rounding (FP64).
+* T-LG: means and variances of GPU HMC chains match the closed form.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1103_4887_gb300 import pimc, synth
+from tests import _linear_gaussian as lgc
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(prob):
+    ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_data(prob.y, prob.I)
+    ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+    return ch
+
+
+@pytest.mark.parametrize("model", ["lg", "hh"])
+def test_hmc_replay_against_oracle(model):
+    if model == "lg":
+        prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
+        L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
+        mu, cov = lgc.posterior(L, r, w)
+        inv_mass = np.diag(cov).copy()
+        eps, n_leap = 0.2, 12
+    else:
+        prob = synth.hh_problem(48, data_seed=2, free=("gNa", "gK", "gL"))
+        inv_mass = np.concatenate([np.tile([5e-3, 5e-5, 5e-5, 5e-5], (prob.M + 1, 1)).T.ravel(),
+                                   1e-2 * np.abs(prob.p_init)])
+        eps, n_leap = 0.1, 8
+    g = pimc.Sampler.from_problem(prob)
+    o = _oracle(prob)
+    agree = 0
+    for t in range(30):
+        X0, p0 = g.state()
+        o.set_path(X0)
+        o.set_params(p0, prob.lo, prob.hi, prob.free)
+        o.set_sweep_counter(t, 1.0)
+        na_g = g.hmc(1, n_leap, eps, inv_mass, seed=5)
+        na_o = o.hmc(1, n_leap, eps, inv_mass, seed=5)
+        Xg, pg = g.state()
+        Xo, po = o.state()
+        if na_g != na_o:
+            pytest.fail(f"trajectory {t}: GPU accepted {na_g}, oracle {na_o}")
+        agree += na_g
+        scale = np.maximum(1.0, np.abs(Xo))
+        assert np.all(np.abs(Xg - Xo) <= 1e-9 * scale), t
+        assert np.all(np.abs(pg - po) <= 1e-9 * np.maximum(1.0, np.abs(po))), t
+    assert agree >= 5  # the chain moves
+
+
+def test_hmc_T_LG_closed_form():
+    prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
+    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
+    mu, cov = lgc.posterior(L, r, w)
+    inv_mass = np.diag(cov).copy()
+    means, vars_ = [], []
+    for k in range(8):
+        g = pimc.Sampler.from_problem(prob)
+        g.set_chain(k)
+        g.set_schedule(n_init=200, n_skip=1)
+        nacc = g.hmc(200 + 6000, 16, 0.2, inv_mass, seed=9)
+        assert nacc > 0.8 * 6200
+        m, v, J = g.moments()
+        assert J == 6000
+        means.append(m)
+        vars_.append(v)
+    means, vars_ = np.array(means), np.array(vars_)
+    se_m = means.std(0, ddof=1) / np.sqrt(len(means))
+    se_v = vars_.std(0, ddof=1) / np.sqrt(len(vars_))
+    assert np.all(np.abs(means.mean(0) - mu) < 4.5 * se_m)
+    assert np.all(np.abs(vars_.mean(0) - np.diag(cov)) < 4.5 * se_v)
+
+
+def test_param_trace_matches_per_sweep_state():
+    prob = synth.hh_problem(200, data_seed=1)
+    g = pimc.Sampler.from_problem(prob)
+    g.set_param_trace(16)
+    ps = []
+    for _ in range(25):
+        g.sweep(1, 3)
+        ps.append(g.state()[1])
+    tr = g.param_trace()
+    assert tr.shape == (16, 7)
+    np.testing.assert_array_equal(tr, np.array(ps[-16:]))
