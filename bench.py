@@ -226,6 +226,42 @@ def run_sweep_M(args):
         print(json.dumps(row), flush=True)
 
 
+def run_batch(args):
+    """Many chains in one launch: 64 seeded HH data sets with M uniform in
+    [2048, 65536] and true (gNa, gK, gL) within +-20 % of nominal, 8 chains each
+    (512 chains), FP32-mixed, tile shape chosen by the autotuner; device time of
+    a block of sweeps (every chain advances by `steps` sweeps)."""
+    import torch
+    from paper_1103_4887_gb300 import pimc, synth
+    rng = np.random.default_rng(2024)
+    n_sets, per_set = 64, 8
+    Ms = rng.integers(2048, 65537, size=n_sets)
+    samplers = []
+    for d in range(n_sets):
+        q = synth.HH_TRUTH.copy()
+        q[:3] *= 1.0 + 0.2 * rng.uniform(-1.0, 1.0, 3)
+        prob = synth.hh_problem(int(Ms[d]), data_seed=100 + d, free=("gNa", "gK", "gL"), p_true=q)
+        for k in range(per_set):
+            s = pimc.Sampler.from_problem(prob, precision=pimc.FP32_MIXED)
+            s.set_chain(k)
+            s.set_schedule(n_init=10 ** 6, n_skip=20, f_acc=0.4, alpha=0.5)
+            samplers.append(s)
+    b = pimc.Batch(samplers)
+    nt, k = b.autotune(4, SEED)
+    steps = max(args.steps // 30, 20)
+    b.sweep(steps, SEED)  # warm-up: also captures the graph of a `steps`-sweep block
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.sweep(steps, SEED)
+    el = time.perf_counter() - t0
+    sites = int(sum(int(m) + 1 for m in Ms)) * per_set
+    n_ctas, _ = b.info()
+    print(json.dumps({"mode": "batch", "chains": n_sets * per_set, "data_sets": n_sets, "sites_per_sweep": sites,
+                      "sweeps": steps, "seconds": el, "site_updates_per_s": sites * steps / el,
+                      "ms_per_sweep_all_chains": 1e3 * el / steps, "tuning": {"threads_per_cta": nt,
+                      "ctas_per_sm": k, "ctas": n_ctas}, "precision": "fp32mixed"}), flush=True)
+
+
 def run_ess(args):
     """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
     all 7 parameters free): checkerboard Metropolis in FP32-mixed and FP64, and
@@ -300,6 +336,8 @@ def main():
     ap.add_argument("--sweep-M", action="store_true",
                     help="observation-length sweep M = 2^10..2^20: site-updates/s and roofline per M, FP32-mixed "
                          "and FP64, with the serial oracle timed on the host for the same M")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched launch: 64 data sets (M ~ U[2048, 65536]) x 8 chains, FP32-mixed, autotuned")
     ap.add_argument("--ess", action="store_true",
                     help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
     args = ap.parse_args()
@@ -315,6 +353,9 @@ def main():
         return
     if args.ess:
         run_ess(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
 
     import torch

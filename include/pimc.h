@@ -202,6 +202,19 @@ int pimc_param_delta(pimc_t h, int l, double pl_new, double beta, double* dA_out
 /* mean, var: D*(M+1)+Np doubles each (path components in SoA order, then p);
  * var is the unbiased sample variance.  n_samples may be NULL. */
 int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples);
+/* Moments of the residuals of the recorded paths (Sec. 6: for a correct model
+ * their means vanish and their variances match 1/Rf and 1/Rm): mean and var
+ * hold (D+1)*M doubles, eps_{n+1,a} = x_{n+1,a} - f_a(x_n) at [a*M + n]
+ * (n = 0..M-1) and delta_n = x_{n,0} - y_n at [D*M + n - 1] (n = 1..M). */
+int pimc_residual_moments(pimc_t h, double* mean, double* var, int64_t* n_samples);
+/* Ensemble forecast from the current state (Sec. 6): n_ens members integrate
+ * x_{k+1} = f(x_k, p; I_future[k]) + xi_k from x_M for n_steps steps, with
+ * model noise xi_{k,a} ~ N(0, 1/Rf_a) when noise != 0 (none where Rf_a = 0);
+ * normals are Philox draws keyed by (member, step, kind 4 | pair, chain).
+ * out (host): n_ens * D * (n_steps+1) doubles, [member][component][step].
+ * Synchronous. */
+int pimc_forecast(pimc_t h, int64_t n_steps, const double* I_future, int n_ens, int noise, uint64_t seed,
+                  double* out);
 /* Histograms of n_sel components (index c < D*(M+1) selects X[c], otherwise
  * p[c - D*(M+1)]): n_bins equal bins on [lo, hi) plus under/overflow slots.
  * 1 <= n_sel <= 64, 1 <= n_bins <= 4096.  Clears the counts. */
@@ -232,6 +245,38 @@ int pimc_accept_stats(pimc_t h, uint64_t* site_acc, uint64_t* site_prop, uint64_
                       uint64_t* par_prop);
 /* Launch geometry chosen for the sweep kernel (grid CTAs, threads per CTA). */
 int pimc_launch_info(pimc_t h, int* grid, int* block);
+
+/* ---- batched launch: many chains and data sets of uneven M ----------------- */
+
+typedef struct pimc_batch_s* pimc_batch_t;
+
+/* Group n handles (same model, precision and device; data and parameters set)
+ * into one launch.  Every CTA owns whole chains and runs them one after
+ * another with CTA-local synchronisation (no grid barrier); chains are
+ * assigned to CTAs longest-first onto the least loaded CTA, with a chain's
+ * cost (M + 1)(1 + free parameters).  Each chain keeps its own handle: state,
+ * schedule, statistics, trace and checkpoints are read and set through it.
+ * Handles must have no work in flight and must not be used while a batch
+ * sweep runs (call pimc_batch_sync first).  A chain runs exactly the sweeps it
+ * would run alone with pimc_set_grid(h, 1) (bit-identical).  The handles must
+ * outlive the batch. */
+int pimc_batch_create(pimc_batch_t* out, const pimc_t* handles, int n);
+int pimc_batch_destroy(pimc_batch_t b);
+const char* pimc_batch_last_error(pimc_batch_t b);
+/* n_sweeps sweeps of every chain (Philox key `seed`; counters continue each
+ * chain's own sweep counter).  Enqueued on the first handle's stream as a
+ * CUDA graph of launches of at most 256 sweeps each (re-captured when n_sweeps
+ * or seed change). */
+int pimc_batch_sweep(pimc_batch_t b, int64_t n_sweeps, uint64_t seed);
+int pimc_batch_sync(pimc_batch_t b);
+/* Tile shape: threads per CTA (128 or 256) and resident CTAs per SM (0 = as
+ * many as fit), i.e. how many chains share a CTA. */
+int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm);
+int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta);
+/* Time trial_sweeps real sweeps (they advance every chain: run this during
+ * burn-in) for each tile shape and keep the fastest; the choice is cached per
+ * process for batches of the same model, precision, size and chain count. */
+int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm);
 
 /* ---- checkpoint / resume ------------------------------------------------------ */
 /* Binary file with a version and a CRC: sizes, settings, path, p, steps,

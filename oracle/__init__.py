@@ -103,6 +103,9 @@ def _declare(L):
     L.orc_set_histograms.argtypes = [_vp, _int, _vp, _vp, _vp, _int]
     L.orc_histograms.argtypes = [_vp, _vp]
     L.orc_hmc.argtypes = [_vp, _i64, _int, _d, _vp, _u64, _vp]
+    L.orc_residual_moments.argtypes = [_vp, _vp, _vp]
+    L.orc_residual_moments.restype = _i64
+    L.orc_forecast.argtypes = [_vp, _i64, _vp, _int, _int, _u64, _vp]
     L.orc_fill_site_uniforms.argtypes = [_u64, _u32, _i64, _i64, _u64, _i64, _vp]
     L.orc_set_state_box.argtypes = [_vp, _vp, _vp]
     L.orc_site_update.argtypes = [_vp, _i64, _vp, _d]
@@ -326,6 +329,18 @@ class Chain:
         var = np.zeros(nc)
         J = lib().orc_moments(self._h, _p(mean), _p(var))
         return mean, var, int(J)
+
+    def residual_moments(self):
+        nr = (self.D + 1) * self.M
+        mean = np.zeros(nr)
+        var = np.zeros(nr)
+        J = lib().orc_residual_moments(self._h, _p(mean), _p(var))
+        return mean, var, int(J)
+
+    def forecast(self, n_steps, I, n_ens, noise, seed):
+        out = np.zeros(n_ens * self.D * (n_steps + 1))
+        lib().orc_forecast(self._h, int(n_steps), _p(_f64(I)), int(n_ens), int(noise), int(seed), _p(out))
+        return out.reshape(n_ens, self.D, n_steps + 1)
 
     def set_histograms(self, comp, lo, hi, n_bins):
         comp = np.ascontiguousarray(comp, dtype=np.int64)

@@ -334,6 +334,7 @@ struct orc_state {
     /* statistics */
     int64_t J;
     double *S1, *S2, *shift;   /* D*(M+1)+Np each */
+    double *E1, *E2;           /* residual sums: eps_{n+1,a} at [a*M+n], delta_n at [D*M+n-1] */
     int n_sel, n_bins;
     int64_t* h_comp;
     double *h_lo, *h_hi;
@@ -377,6 +378,8 @@ orc_state* orc_create(int model, int64_t M, double dt, double Rm, const double* 
     s->S1 = (double*)calloc((size_t)(nc + Np), sizeof(double));
     s->S2 = (double*)calloc((size_t)(nc + Np), sizeof(double));
     s->shift = (double*)calloc((size_t)(nc + Np), sizeof(double));
+    s->E1 = (double*)calloc((size_t)((D + 1) * M), sizeof(double));
+    s->E2 = (double*)calloc((size_t)((D + 1) * M), sizeof(double));
     s->n_skip = 1; s->n_init = 0; s->n_cool = 0;
     s->beta0 = 1.0; s->fbeta = 1.0; s->beta = 1.0; s->f_acc = 0.4; s->alpha = 0.0;
     for (int l = 0; l < ORC_MAXP; ++l) { s->lo[l] = -INFINITY; s->hi[l] = INFINITY; }
@@ -388,7 +391,7 @@ void orc_destroy(orc_state* s)
 {
     if (!s) return;
     free(s->y); free(s->I); free(s->X); free(s->f); free(s->sig); free(s->acc_win);
-    free(s->site_margin); free(s->S1); free(s->S2); free(s->shift);
+    free(s->site_margin); free(s->S1); free(s->S2); free(s->shift); free(s->E1); free(s->E2);
     free(s->h_comp); free(s->h_lo); free(s->h_hi); free(s->h_counts);
     free(s);
 }
@@ -611,6 +614,20 @@ static void orc_record(orc_state* s)
         s->S2[c] += d * d;
     }
     s->J += 1;
+    /* residuals of the recorded path (Sec. 6: their means should vanish and
+     * their variances match the assumed noise): eps_{n+1} = x_{n+1} - f(x_n),
+     * delta_n = x_{n,0} - y_n */
+    for (int64_t n = 0; n < s->M; ++n)
+        for (int a = 0; a < s->D; ++a) {
+            double e = XI(s, a, n + 1) - FI(s, a, n);
+            s->E1[(int64_t)a * s->M + n] += e;
+            s->E2[(int64_t)a * s->M + n] += e * e;
+        }
+    for (int64_t n = 1; n <= s->M; ++n) {
+        double d = XI(s, 0, n) - s->y[n];
+        s->E1[(int64_t)s->D * s->M + n - 1] += d;
+        s->E2[(int64_t)s->D * s->M + n - 1] += d * d;
+    }
     for (int k = 0; k < s->n_sel; ++k) {
         double v = orc_component(s, s->h_comp[k]);
         int64_t slot;
@@ -635,6 +652,49 @@ int64_t orc_moments(const orc_state* s, double* mean, double* var)
         var[c] = s->J > 1 ? (s->S2[c] - s->S1[c] * s->S1[c] / J) / (J - 1.0) : NAN;
     }
     return s->J;
+}
+
+int64_t orc_residual_moments(const orc_state* s, double* mean, double* var)
+{
+    int64_t nr = (int64_t)(s->D + 1) * s->M;
+    double J = (double)s->J;
+    for (int64_t i = 0; i < nr; ++i) {
+        mean[i] = s->J > 0 ? s->E1[i] / J : NAN;
+        var[i] = s->J > 1 ? (s->E2[i] - s->E1[i] * s->E1[i] / J) / (J - 1.0) : NAN;
+    }
+    return s->J;
+}
+
+/* Ensemble forecast from the current state (Sec. 6): member e integrates
+ * x_{k+1} = f(x_k, p; I_k) + xi_k with xi_{k,a} ~ N(0, 1/Rf_a) (none where
+ * Rf_a = 0, or for every member when noise == 0), starting at x_M; normals are
+ * Philox draws keyed by (member, step, kind 4 | pair, chain).
+ * out[e][a][k], k = 0..n_steps. */
+void orc_forecast(const orc_state* s, int64_t n_steps, const double* I, int n_ens, int noise, uint64_t seed,
+                  double* out)
+{
+    double x[ORC_MAXD], fx[ORC_MAXD];
+    for (int e = 0; e < n_ens; ++e) {
+        double* o = out + (int64_t)e * s->D * (n_steps + 1);
+        for (int a = 0; a < s->D; ++a) { x[a] = XI(s, a, s->M); o[(int64_t)a * (n_steps + 1)] = x[a]; }
+        for (int64_t k = 0; k < n_steps; ++k) {
+            orc_model_map(s->model, s->dt, x, s->p, I[k], fx);
+            for (int pair = 0; 2 * pair < s->D; ++pair) {
+                uint32_t w[4];
+                double z0 = 0.0, z1 = 0.0;
+                if (noise) {
+                    orc_block(seed, s->chain, (uint64_t)k, (uint32_t)e, ORC_KIND_FORECAST, (uint32_t)pair, w);
+                    orc_box_muller(orc_u01(w[0], w[1]), orc_u01(w[2], w[3]), &z0, &z1);
+                }
+                for (int q = 0; q < 2 && 2 * pair + q < s->D; ++q) {
+                    int a = 2 * pair + q;
+                    double z = q == 0 ? z0 : z1;
+                    fx[a] += (noise && s->Rf[a] > 0.0) ? z / sqrt(s->Rf[a]) : 0.0;
+                }
+            }
+            for (int a = 0; a < s->D; ++a) { x[a] = fx[a]; o[(int64_t)a * (n_steps + 1) + k + 1] = x[a]; }
+        }
+    }
 }
 
 int orc_set_histograms(orc_state* s, int n_sel, const int64_t* comp, const double* lo,

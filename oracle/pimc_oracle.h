@@ -42,7 +42,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Open-interval uniform from two 32-bit words: ((hi>>6)*2^26 + (lo>>6) + 0.5) * 2^-52 */
 double orc_u01(uint32_t hi, uint32_t lo);
 /* Draw kinds used in the counter's third word (kind << 24 | block). */
-enum { ORC_KIND_SITE = 0, ORC_KIND_PARAM = 1, ORC_KIND_HMC_MOM = 2, ORC_KIND_HMC_ACC = 3 };
+enum { ORC_KIND_SITE = 0, ORC_KIND_PARAM = 1, ORC_KIND_HMC_MOM = 2, ORC_KIND_HMC_ACC = 3, ORC_KIND_FORECAST = 4 };
 /* Site draw: D normals (Box-Muller, cos then sin per pair) and one uniform. */
 void orc_site_draws(uint64_t seed, uint32_t chain, uint64_t sweep, int64_t n, int D,
                     double* z, double* u);
@@ -101,6 +101,11 @@ void orc_accept_stats(const orc_state* s, uint64_t* site_acc /*2: even, odd*/,
 
 /* Running moments of every path component and parameter (Sec. 4.1): returns J. */
 int64_t orc_moments(const orc_state* s, double* mean, double* var);
+/* Moments of the residuals eps_{n+1,a} ([a*M+n]) and delta_n ([D*M+n-1]) of the recorded paths. */
+int64_t orc_residual_moments(const orc_state* s, double* mean, double* var);
+/* Ensemble forecast from the current state; out[e][a][k], k = 0..n_steps. */
+void orc_forecast(const orc_state* s, int64_t n_steps, const double* I, int n_ens, int noise, uint64_t seed,
+                  double* out);
 int  orc_set_histograms(orc_state* s, int n_sel, const int64_t* comp, const double* lo,
                         const double* hi, int n_bins);
 void orc_histograms(const orc_state* s, uint64_t* counts);

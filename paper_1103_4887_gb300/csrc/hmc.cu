@@ -169,15 +169,22 @@ __global__ void __launch_bounds__(kBlock) hmc_record_kernel(Ctx c)
     if (!(s >= c.n_init && (s - c.n_init) % c.n_skip == 0)) return;
     const int64_t n0 = (int64_t)blockIdx.x * kBlock;
     const int64_t n1 = min(n0 + (int64_t)kBlock, c.M + 1);
-    record_sample<Model, R>(c, n0, n1, blockIdx.x == 0, c.st->p, c.st->J == 0, threadIdx.x, kBlock);
+    record_sample<Model, R>(c, n0, n1, blockIdx.x == 0, c.st->p, c.st->J == 0, threadIdx.x, kBlock,
+                            (const R*)c.F[c.st->fidx]);
 }
 
+// Counters after a trajectory; the parameter trace gets the end state.
+template <int NP>
 __global__ void hmc_tick_kernel(Ctx c)
 {
     DevState* g = c.st;
     const long long s = g->sweep;
     if (s >= c.n_init && (s - c.n_init) % c.n_skip == 0) g->J += 1;
     g->sweep = s + 1;
+    if (c.trace) {
+        for (int l = 0; l < NP; ++l) c.trace[(g->tr_n % c.trace_cap) * NP + l] = g->p[l];
+        g->tr_n += 1;
+    }
 }
 
 template <class Model, class R>
@@ -211,7 +218,7 @@ static cudaError_t hmc_traj_t(const Ctx& c, const HmcBuffers& b, int n_leap, dou
     hmc_commit_kernel<Model, R><<<ge, 256, 0, s>>>(c, b.hs, b.Q);
     if ((e = launch_refresh_cache(ModelId<Model>::value, prec_of<R>(), c, s)) != cudaSuccess) return e;
     hmc_record_kernel<Model, R><<<(unsigned)((c.M + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(c);
-    hmc_tick_kernel<<<1, 1, 0, s>>>(c);
+    hmc_tick_kernel<NP><<<1, 1, 0, s>>>(c);
     return cudaGetLastError();
 }
 

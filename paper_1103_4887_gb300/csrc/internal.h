@@ -47,6 +47,7 @@ struct Ctx {
     unsigned* ticket;             // last-block counter of single-pass reductions
     double* red;                  // [kMaxGrid * 8] per-CTA partials of single-pass reductions
     double *S1, *S2, *shift;      // [D*(M+1) + NP] running shifted sums (FP64)
+    double *R1, *R2;              // [(D+1)*M] residual sums: eps_{n+1,a} at a*M+n, delta_n at D*M+n-1
     unsigned long long* hist;     // [n_sel][n_bins + 2]
     const int64_t* h_comp;
     const double *h_lo, *h_hi;
@@ -86,6 +87,11 @@ void set_thread_error(const char* msg);
 // Kernel launchers (model: pimc_model, prec: pimc_precision).
 cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s);
 int sweep_max_grid(int model, int prec, int device);  // co-resident CTAs on the device
+// Many whole chains in one launch (nt threads per CTA: 128 or 256): CTA b runs
+// chains[order[first[b] .. first[b+1])] one after another.
+cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first, const int* order,
+                               int n_ctas, int64_t n_sweeps, uint64_t seed, cudaStream_t s);
+int batch_ctas_per_sm(int model, int prec, int nt);
 cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s);
 cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s);
 // out: 3 doubles (A, Ao, Af).  X_ext/p_ext: FP64 caller arrays ([D][M+1] dense, [NP]) or null
@@ -100,6 +106,9 @@ cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double 
                                double* out, cudaStream_t s);
 // dst[i] = (storage type) src[i], i < n.
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s);
+// Ensemble forecast from the current state: out[e][a][k] (device, FP64).
+cudaError_t launch_forecast(int model, int prec, const Ctx& c, int64_t n_steps, const double* I, int n_ens,
+                            int noise, uint64_t seed, double* out, cudaStream_t s);
 // X conversion between the handle storage and dense FP64 [D][M+1].
 cudaError_t launch_path_io(int prec, const Ctx& c, int D, double* dense, int to_state, cudaStream_t s);
 

@@ -162,6 +162,50 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(Ctx c, const double* Xe, c
         for (int l = 0; l < NP; ++l) gp[l] = res[l];
 }
 
+// Ensemble forecast (Sec. 6): member e (one thread) integrates
+// x_{k+1} = f(x_k, p; I_k) + xi_k, xi_{k,a} ~ N(0, 1/Rf_a) (none where Rf_a = 0 or
+// when noise == 0) from the current x_M; normals are Philox draws keyed by
+// (member, step, kind 4 | pair, chain).
+template <class Model, class R>
+__global__ void forecast_kernel(Ctx c, int64_t n_steps, const double* I, int n_ens, int noise, uint64_t seed,
+                                double* out)
+{
+    constexpr int D = Model::D;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_ens) return;
+    R q[kMaxP], x[D], fx[D];
+    Model::prep(c.st->p, q);
+    const R* X = (const R*)c.X;
+    double* o = out + (int64_t)e * D * (n_steps + 1);
+    for (int a = 0; a < D; ++a) {
+        x[a] = X[a * c.ldx + c.M];
+        o[(int64_t)a * (n_steps + 1)] = (double)x[a];
+    }
+    for (int64_t k = 0; k < n_steps; ++k) {
+        rk4_map<Model, R>(x, q, R(I[k]), R(c.dt), fx);
+        if (noise) {
+            for (int pair = 0; 2 * pair < D; ++pair) {
+                double z0, z1;
+                Num<double>::box_muller(draw_block(seed, c.chain, (uint64_t)k, (uint32_t)e, 4u, (uint32_t)pair), z0, z1);
+                if (c.Rf[2 * pair] > 0.0) fx[2 * pair] += R(z0 / sqrt(c.Rf[2 * pair]));
+                if (2 * pair + 1 < D && c.Rf[2 * pair + 1] > 0.0) fx[2 * pair + 1] += R(z1 / sqrt(c.Rf[2 * pair + 1]));
+            }
+        }
+        for (int a = 0; a < D; ++a) {
+            x[a] = fx[a];
+            o[(int64_t)a * (n_steps + 1) + k + 1] = (double)x[a];
+        }
+    }
+}
+
+template <class Model, class R>
+static cudaError_t forecast_t(const Ctx& c, int64_t n_steps, const double* I, int n_ens, int noise, uint64_t seed,
+                              double* out, cudaStream_t s)
+{
+    forecast_kernel<Model, R><<<(n_ens + 127) / 128, 128, 0, s>>>(c, n_steps, I, n_ens, noise, seed, out);
+    return cudaGetLastError();
+}
+
 template <class R>
 __global__ void convert_kernel(const double* src, R* dst, int64_t n)
 {
@@ -243,6 +287,12 @@ cudaError_t launch_grad(int model, int prec, const Ctx& c, const double* X_ext, 
 {
     PIMC_DISPATCH(grad_t, c, X_ext, p_ext, beta, gX, gp, s);
 }
+cudaError_t launch_forecast(int model, int prec, const Ctx& c, int64_t n_steps, const double* I, int n_ens,
+                            int noise, uint64_t seed, double* out, cudaStream_t s)
+{
+    PIMC_DISPATCH(forecast_t, c, n_steps, I, n_ens, noise, seed, out, s);
+}
+
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s)
 {
     const unsigned grid = (unsigned)((n + 255) / 256);

@@ -2,8 +2,11 @@
 // buffers, argument validation, launch geometry, statistics read-back and
 // checkpoints.  All arithmetic of the sampler runs in the kernels of sweep.cu
 // and ops.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <map>
+#include <queue>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -34,6 +37,7 @@ struct pimc_handle_s {
     unsigned* ticket = nullptr;
     double* red = nullptr;
     double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
+    double *R1 = nullptr, *R2 = nullptr;
     unsigned long long* hist = nullptr;
     int64_t* h_comp = nullptr;
     double *h_lo = nullptr, *h_hi = nullptr;
@@ -101,6 +105,7 @@ Ctx make_ctx(pimc_t h)
     c.acc_win = h->acc_win; c.st = h->st; c.partials = h->partials; c.bar = h->bar;
     c.ticket = h->ticket; c.red = h->red;
     c.S1 = h->S1; c.S2 = h->S2; c.shift = h->shift;
+    c.R1 = h->R1; c.R2 = h->R2;
     c.hist = h->hist; c.h_comp = h->h_comp; c.h_lo = h->h_lo; c.h_hi = h->h_hi;
     c.n_sel = h->n_sel; c.n_bins = h->n_bins;
     c.trace = h->trace; c.trace_cap = h->trace_cap;
@@ -213,7 +218,7 @@ void free_all(pimc_t h)
 {
     void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar,
                     h->ticket, h->red, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
-                    h->dense, h->small, h->y64, h->I64, h->trace, h->hmc.hs, h->hmc.Q, h->hmc.P,
+                    h->dense, h->small, h->y64, h->I64, h->trace, h->R1, h->R2, h->hmc.hs, h->hmc.Q, h->hmc.P,
                     h->hmc.g, h->hmc.invm};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -228,6 +233,8 @@ int reset_stats(pimc_t h)
     CK(h, cudaMemset(h->S2, 0, sizeof(double) * nc));
     CK(h, cudaMemset(h->shift, 0, sizeof(double) * nc));
     CK(h, cudaMemset(h->acc_win, 0, sizeof(uint32_t) * h->ldx));
+    CK(h, cudaMemset(h->R1, 0, sizeof(double) * (h->D + 1) * h->M));
+    CK(h, cudaMemset(h->R2, 0, sizeof(double) * (h->D + 1) * h->M));
     if (h->hist) CK(h, cudaMemset(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
     return PIMC_OK;
 }
@@ -291,6 +298,8 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         {(void**)&h->shift, sizeof(double) * nc},
         {(void**)&h->dense, sizeof(double) * D * (M + 1)},
         {(void**)&h->small, sizeof(double) * 16},
+        {(void**)&h->R1, sizeof(double) * (D + 1) * M},
+        {(void**)&h->R2, sizeof(double) * (D + 1) * M},
         {(void**)&h->y64, sizeof(double) * (M + 1)},
         {(void**)&h->I64, sizeof(double) * M},
     };
@@ -613,6 +622,47 @@ int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples)
     return PIMC_OK;
 }
 
+int pimc_residual_moments(pimc_t h, double* mean, double* var, int64_t* n_samples)
+{
+    if (!h) return PIMC_ERR_ARG;
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    const int64_t nr = (int64_t)(h->D + 1) * h->M;
+    std::vector<double> R1(nr), R2(nr);
+    CK(h, cudaMemcpy(R1.data(), h->R1, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(R2.data(), h->R2, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+    const double J = (double)h->hs.J;
+    for (int64_t i = 0; i < nr; ++i) {
+        if (mean) mean[i] = h->hs.J > 0 ? R1[i] / J : NAN;
+        if (var) var[i] = h->hs.J > 1 ? (R2[i] - R1[i] * R1[i] / J) / (J - 1.0) : NAN;
+    }
+    if (n_samples) *n_samples = h->hs.J;
+    return PIMC_OK;
+}
+
+int pimc_forecast(pimc_t h, int64_t n_steps, const double* I_future, int n_ens, int noise, uint64_t seed,
+                  double* out)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_forecast before data/params");
+    if (n_steps < 0 || n_ens < 1 || !out || (n_steps > 0 && !I_future))
+        return fail(h, PIMC_ERR_ARG, "bad forecast arguments");
+    if (!check_finite(I_future, n_steps)) return fail(h, PIMC_ERR_ARG, "I_future has non-finite values");
+    const size_t nout = (size_t)n_ens * h->D * (n_steps + 1);
+    double *dI = nullptr, *dout = nullptr;
+    CK(h, cudaMalloc(&dI, sizeof(double) * std::max<int64_t>(n_steps, 1)));
+    cudaError_t e = cudaMalloc(&dout, sizeof(double) * nout);
+    if (e == cudaSuccess && n_steps > 0)
+        e = cudaMemcpyAsync(dI, I_future, sizeof(double) * n_steps, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_forecast(h->model, h->prec, make_ctx(h), n_steps, dI, n_ens, noise, seed, dout, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dI);
+    if (dout) cudaFree(dout);
+    CK(h, e);
+    return PIMC_OK;
+}
+
 int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const double* lo, const double* hi, int n_bins)
 {
     if (!h) return PIMC_ERR_ARG;
@@ -897,7 +947,7 @@ struct Reader {
 };
 
 const char kMagic[8] = {'P', 'I', 'M', 'C', 'C', 'K', 'P', 'T'};
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;
 
 }  // namespace
 
@@ -946,6 +996,14 @@ extern "C" int pimc_checkpoint_save(pimc_t h, const char* path)
     w.put(S1.data(), sizeof(double) * nc);
     w.put(S2.data(), sizeof(double) * nc);
     w.put(SH.data(), sizeof(double) * nc);
+    {
+        const int64_t nr = (int64_t)(h->D + 1) * h->M;
+        std::vector<double> R1(nr), R2(nr);
+        CK(h, cudaMemcpy(R1.data(), h->R1, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(R2.data(), h->R2, sizeof(double) * nr, cudaMemcpyDeviceToHost));
+        w.put(R1.data(), sizeof(double) * nr);
+        w.put(R2.data(), sizeof(double) * nr);
+    }
     w.val(h->n_sel); w.val(h->n_bins);
     if (h->n_sel > 0) {
         w.put(hc.data(), sizeof(int64_t) * hc.size());
@@ -1002,6 +1060,9 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
          rd.get(F0.data(), sizeof(double) * F0.size()) && rd.get(F1.data(), sizeof(double) * F1.size()) &&
          rd.get(acc.data(), sizeof(uint32_t) * n1) && rd.get(S1.data(), sizeof(double) * nc) &&
          rd.get(S2.data(), sizeof(double) * nc) && rd.get(SH.data(), sizeof(double) * nc);
+    const int64_t nr = (int64_t)(D + 1) * M;
+    std::vector<double> R1(nr), R2(nr);
+    ok = ok && rd.get(R1.data(), sizeof(double) * nr) && rd.get(R2.data(), sizeof(double) * nr);
     int n_sel = 0, n_bins = 0;
     ok = ok && rd.val(n_sel) && rd.val(n_bins);
     if (!ok) return fail(h, PIMC_ERR_IO, "%s: truncated payload", path);
@@ -1041,6 +1102,8 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
     CK(h, cudaMemcpy(h->S1, S1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->S2, S2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->shift, SH.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->R1, R1.data(), sizeof(double) * nr, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->R2, R2.data(), sizeof(double) * nr, cudaMemcpyHostToDevice));
     if (n_sel > 0) {
         if ((r = pimc_set_histograms(h, n_sel, hc.data(), hl.data(), hh.data(), n_bins)) != PIMC_OK) return r;
         CK(h, cudaMemcpy(h->hist, hist.data(), sizeof(unsigned long long) * hist.size(), cudaMemcpyHostToDevice));
@@ -1053,3 +1116,286 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
     choose_grid(h);
     return push_state(h);
 }
+
+// ---------------------------------------------------------------------------
+// Batched launch of many chains (independent data sets and/or chains).
+// ---------------------------------------------------------------------------
+struct pimc_batch_s {
+    std::vector<pimc_t> hs;
+    int model = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    Ctx* d_ctx = nullptr;
+    int* d_first = nullptr;
+    int* d_order = nullptr;
+    int n_ctas = 0, nt = 256, ctas_per_sm = 0;
+    std::vector<unsigned> versions;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_sweeps = -1;
+    uint64_t graph_seed = 0;
+    bool dirty = true;
+    std::string err;
+};
+
+namespace {
+
+int bfail(pimc_batch_t b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define BCK(b, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? PIMC_ERR_OOM : PIMC_ERR_CUDA, \
+                         "%s: %s", #call, cudaGetErrorString(e_));                            \
+    } while (0)
+
+// Work of one sweep of a chain: sites x (1 + free parameters).
+double chain_cost(pimc_t h)
+{
+    int nf = 0;
+    for (int l = 0; l < h->NP; ++l) nf += (h->hs.free_mask >> l) & 1u;
+    return (double)(h->M + 1) * (double)(1 + nf);
+}
+
+// Contexts of all chains and a longest-processing-time-first assignment of
+// whole chains to CTAs (each chain to the currently least loaded CTA).
+int batch_build(pimc_batch_t b)
+{
+    const int n = (int)b->hs.size();
+    int dev = b->hs[0]->device, sms = b->hs[0]->num_sms;
+    (void)dev;
+    int occ = batch_ctas_per_sm(b->model, b->prec, b->nt);
+    if (occ < 1) return bfail(b, PIMC_ERR_CUDA, "batched kernel cannot be resident (nt = %d)", b->nt);
+    int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+    b->n_ctas = std::max(1, std::min(n, per_sm * sms));
+    std::vector<Ctx> ctx(n);
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) {
+        ctx[i] = make_ctx(b->hs[i]);
+        idx[i] = i;
+        b->versions[i] = b->hs[i]->ctx_version;
+    }
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int c) { return chain_cost(b->hs[a]) > chain_cost(b->hs[c]); });
+    typedef std::pair<double, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int k = 0; k < b->n_ctas; ++k) pq.push(Load(0.0, k));
+    std::vector<std::vector<int>> per(b->n_ctas);
+    for (int i : idx) {
+        Load l = pq.top();
+        pq.pop();
+        per[l.second].push_back(i);
+        l.first += chain_cost(b->hs[i]);
+        pq.push(l);
+    }
+    std::vector<int> first(b->n_ctas + 1, 0), order;
+    order.reserve(n);
+    for (int k = 0; k < b->n_ctas; ++k) {
+        first[k] = (int)order.size();
+        for (int i : per[k]) order.push_back(i);
+    }
+    first[b->n_ctas] = (int)order.size();
+    if (b->d_ctx) cudaFree(b->d_ctx);
+    if (b->d_first) cudaFree(b->d_first);
+    if (b->d_order) cudaFree(b->d_order);
+    b->d_ctx = nullptr; b->d_first = nullptr; b->d_order = nullptr;
+    BCK(b, cudaMalloc(&b->d_ctx, sizeof(Ctx) * n));
+    BCK(b, cudaMalloc(&b->d_first, sizeof(int) * (b->n_ctas + 1)));
+    BCK(b, cudaMalloc(&b->d_order, sizeof(int) * n));
+    BCK(b, cudaMemcpy(b->d_ctx, ctx.data(), sizeof(Ctx) * n, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_first, first.data(), sizeof(int) * (b->n_ctas + 1), cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->dirty = false;
+    return PIMC_OK;
+}
+
+std::map<std::pair<int, int>, std::pair<int, int>>& tune_cache()
+{
+    static std::map<std::pair<int, int>, std::pair<int, int>> m;
+    return m;
+}
+
+int tune_key_sites(pimc_batch_t b)
+{
+    double tot = 0.0;
+    for (pimc_t h : b->hs) tot += chain_cost(h);
+    return (int)std::log2(std::max(1.0, tot)) * 16 + b->model * 4 + b->prec;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pimc_batch_create(pimc_batch_t* out, const pimc_t* handles, int n)
+{
+    if (!out || !handles || n < 1) return bfail(nullptr, PIMC_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    pimc_batch_t b = new pimc_batch_s();
+    for (int i = 0; i < n; ++i) {
+        pimc_t h = handles[i];
+        if (!h) { delete b; return bfail(nullptr, PIMC_ERR_ARG, "handle %d is NULL", i); }
+        if (!h->have_data || !h->have_params) { delete b; return bfail(nullptr, PIMC_ERR_STATE, "handle %d has no data/params", i); }
+        if (i > 0 && (h->model != handles[0]->model || h->prec != handles[0]->prec || h->device != handles[0]->device)) {
+            delete b;
+            return bfail(nullptr, PIMC_ERR_ARG, "handles of a batch must share model, precision and device");
+        }
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess || pull_state(h) != PIMC_OK) {
+            delete b;
+            return bfail(nullptr, PIMC_ERR_CUDA, "handle %d: synchronisation failed", i);
+        }
+        b->hs.push_back(h);
+    }
+    b->model = handles[0]->model;
+    b->prec = handles[0]->prec;
+    b->stream = handles[0]->stream;
+    b->versions.assign(n, ~0u);
+    auto it = tune_cache().find(std::make_pair(tune_key_sites(b), n));
+    if (it != tune_cache().end()) { b->nt = it->second.first; b->ctas_per_sm = it->second.second; }
+    int r = batch_build(b);
+    if (r != PIMC_OK) {
+        g_create_error = b->err;
+        pimc_batch_destroy(b);
+        return r;
+    }
+    *out = b;
+    return PIMC_OK;
+}
+
+int pimc_batch_destroy(pimc_batch_t b)
+{
+    if (!b) return PIMC_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_ctx) cudaFree(b->d_ctx);
+    if (b->d_first) cudaFree(b->d_first);
+    if (b->d_order) cudaFree(b->d_order);
+    delete b;
+    return PIMC_OK;
+}
+
+const char* pimc_batch_last_error(pimc_batch_t b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm)
+{
+    if (!b) return PIMC_ERR_ARG;
+    if (threads_per_cta != 128 && threads_per_cta != 256) return bfail(b, PIMC_ERR_ARG, "threads_per_cta must be 128 or 256");
+    if (ctas_per_sm < 0) return bfail(b, PIMC_ERR_ARG, "ctas_per_sm must be >= 0");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->nt = threads_per_cta;
+    b->ctas_per_sm = ctas_per_sm;
+    return batch_build(b);
+}
+
+int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta)
+{
+    if (!b) return PIMC_ERR_ARG;
+    if (n_ctas) *n_ctas = b->n_ctas;
+    if (threads_per_cta) *threads_per_cta = b->nt;
+    return PIMC_OK;
+}
+
+int pimc_batch_sweep(pimc_batch_t b, int64_t n_sweeps, uint64_t seed)
+{
+    if (!b) return PIMC_ERR_ARG;
+    if (n_sweeps < 0) return bfail(b, PIMC_ERR_ARG, "n_sweeps < 0");
+    for (size_t i = 0; i < b->hs.size(); ++i)
+        if (b->hs[i]->ctx_version != b->versions[i]) b->dirty = true;
+    if (b->dirty) {
+        BCK(b, cudaStreamSynchronize(b->stream));
+        int r = batch_build(b);
+        if (r != PIMC_OK) return r;
+    }
+    if (n_sweeps == 0) return PIMC_OK;
+    // a sweep block is a sequence of launches of <= 256 sweeps each (bounded
+    // kernel duration), captured once as a CUDA graph and replayed
+    const int64_t chunk = 256;
+    if (!b->exec || b->graph_sweeps != n_sweeps || b->graph_seed != seed) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        if (b->stream) {
+            cudaGraph_t graph = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int64_t done = 0; done < n_sweeps && e == cudaSuccess; done += chunk)
+                e = launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
+                                       std::min<int64_t>(chunk, n_sweeps - done), seed, b->stream);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            BCK(b, e);
+            b->graph_sweeps = n_sweeps;
+            b->graph_seed = seed;
+        }
+    }
+    if (b->exec) {
+        BCK(b, cudaGraphLaunch(b->exec, b->stream));
+    } else {
+        for (int64_t done = 0; done < n_sweeps; done += chunk)
+            BCK(b, launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
+                                      std::min<int64_t>(chunk, n_sweeps - done), seed, b->stream));
+    }
+    return PIMC_OK;
+}
+
+int pimc_batch_sync(pimc_batch_t b)
+{
+    if (!b) return PIMC_ERR_ARG;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return PIMC_OK;
+}
+
+int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm)
+{
+    if (!b) return PIMC_ERR_ARG;
+    if (trial_sweeps < 1) return bfail(b, PIMC_ERR_ARG, "trial_sweeps must be >= 1");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_nt = b->nt, best_k = b->ctas_per_sm;
+    const int nts[2] = {128, 256};
+    for (int ni = 0; ni < 2; ++ni) {
+        const int occ = batch_ctas_per_sm(b->model, b->prec, nts[ni]);
+        for (int k = 1; k <= occ; k *= 2) {
+            b->nt = nts[ni];
+            b->ctas_per_sm = k;
+            int r = batch_build(b);
+            if (r != PIMC_OK) return r;
+            BCK(b, cudaEventRecord(e0, b->stream));
+            BCK(b, launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
+                                      trial_sweeps, seed, b->stream));
+            BCK(b, cudaEventRecord(e1, b->stream));
+            BCK(b, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_nt = nts[ni]; best_k = k; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->nt = best_nt;
+    b->ctas_per_sm = best_k;
+    tune_cache()[std::make_pair(tune_key_sites(b), (int)b->hs.size())] = std::make_pair(best_nt, best_k);
+    if (threads_per_cta) *threads_per_cta = best_nt;
+    if (ctas_per_sm) *ctas_per_sm = best_k;
+    return batch_build(b);
+}
+
+}  // extern "C"

@@ -27,10 +27,14 @@ __device__ __forceinline__ void accumulate(const Ctx& c, int64_t ci, double v, b
     c.S2[ci] += d * d;
 }
 
-// Thread t of nt records its share; p is the current parameter vector.
+// Thread t of nt records its share; p is the current parameter vector and Fc
+// the current f cache (f(x_n) for n < M), which gives the model-error
+// residuals eps_{n+1} = x_{n+1} - f(x_n) without another map evaluation; the
+// measurement residuals are delta_n = x_{n,0} - y_n (their statistics are the
+// model check of Sec. 6).
 template <class Model, class R>
 __device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_here, const double* p,
-                              bool first_rec, int t, int nt)
+                              bool first_rec, int t, int nt, const R* Fc)
 {
     constexpr int D = Model::D, NP = Model::NP;
     const int64_t M = c.M, nx = (int64_t)D * (M + 1);
@@ -38,6 +42,19 @@ __device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_
     for (int64_t n = n0 + t; n < n1; n += nt) {
 #pragma unroll
         for (int a = 0; a < D; ++a) accumulate(c, (int64_t)a * (M + 1) + n, (double)X[a * c.ldx + n], first_rec);
+        if (n < M) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const double e = (double)X[a * c.ldx + n + 1] - (double)Fc[a * c.ldf + n];
+                c.R1[(int64_t)a * M + n] += e;
+                c.R2[(int64_t)a * M + n] += e * e;
+            }
+        }
+        if (n >= 1) {
+            const double d = (double)X[n] - (double)((const R*)c.y)[n];
+            c.R1[(int64_t)D * M + n - 1] += d;
+            c.R2[(int64_t)D * M + n - 1] += d * d;
+        }
     }
     if (params_here && t < NP) accumulate(c, nx + t, p[t], first_rec);
     for (int kk = t; kk < c.n_sel; kk += nt) {

@@ -28,7 +28,7 @@ template <class R> struct Coef {
     }
 };
 
-template <class R> struct SweepShared {
+template <class R, int NT> struct SweepShared {
     double p[kMaxP], lo[kMaxP], hi[kMaxP], sigp[kMaxP];
     double beta;
     long long sweep, J;
@@ -39,7 +39,8 @@ template <class R> struct SweepShared {
     int inbox[kMaxP];
     R q_cur[kMaxP];                   // current model parameters in R
     R q_new[kMaxP][kMaxP];            // proposed vector for each parameter move, in R
-    R tpart[kSweepBlock];           // per-thread partial sums of a parameter move
+    R tpart[NT];                    // per-thread partial sums of a parameter move
+    double cta_total;               // CTA sum of a parameter move (CTA-local chains)
     int abort;
     unsigned long long site_acc[2], site_prop[2], nonfinite;
     long long tr_n;
@@ -239,11 +240,48 @@ __device__ __forceinline__ double block_sum(double v, double* wsum)
     return t;
 }
 
-template <class Model, class R>
-__global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
+// Synchronisation policies of a chain's sweep.  GridSync: the chain is tiled
+// over all CTAs of a cooperative launch (grid barriers, every CTA sums all CTA
+// partials in the same order).  BlockSync: one CTA owns the whole chain
+// (CTA barriers, the CTA sum is the total).  With one CTA both give the same
+// bits.
+struct GridSync {
+    __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort) const { return grid_barrier(c, s_abort); }
+    __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, double v, double*) const
+    {
+        c.partials[slot * kMaxGrid + blockIdx.x] = v;
+    }
+    __device__ __forceinline__ double gather(const Ctx& c, unsigned slot, int lane, const double*) const
+    {
+        double v = 0.0;
+        for (int i = lane; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
+        return warp_sum(v);
+    }
+    __device__ __forceinline__ bool lead() const { return blockIdx.x == 0; }
+};
+
+struct BlockSync {
+    __device__ __forceinline__ bool barrier(const Ctx&, int*) const
+    {
+        __syncthreads();
+        return true;
+    }
+    __device__ __forceinline__ void publish(const Ctx&, unsigned, double v, double* total) const { *total = v; }
+    __device__ __forceinline__ double gather(const Ctx&, unsigned, int lane, const double* total) const
+    {
+        return warp_sum(lane == 0 ? *total : 0.0);
+    }
+    __device__ __forceinline__ bool lead() const { return true; }
+};
+
+// n_sweeps checkerboard sweeps of one chain over the sites [n0, n1) this CTA
+// owns: loads the chain's scalar state, runs the sweeps, writes it back (the
+// lead CTA) and adds this CTA's counters.
+template <class Model, class R, int NT, class Sync>
+__device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
+                            const Sync& sync)
 {
-    constexpr int D = Model::D, NP = Model::NP, NT = kSweepBlock;
-    __shared__ SweepShared<R> sh;
+    constexpr int D = Model::D, NP = Model::NP;
     const int tid = threadIdx.x;
     const Coef<R> kc(c);
     if (tid == 0) {
@@ -260,8 +298,6 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
     __syncthreads();
 
     const int64_t M = c.M;
-    const int64_t n0 = (int64_t)blockIdx.x * c.tile;
-    const int64_t n1 = min(n0 + c.tile, M + 1);
     unsigned long long my_acc[2] = {0ull, 0ull}, my_prop[2] = {0ull, 0ull}, my_nf = 0ull;
     R* X = (R*)c.X;
     R* sig = (R*)c.sig;
@@ -303,7 +339,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
                 my_acc[parity] += site_move<Model, R>(c, kc, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
                 my_prop[parity] += 1ull;
             }
-            if (!grid_barrier(c, &sh.abort)) goto done;
+            if (!sync.barrier(c, &sh.abort)) goto done;
         }
 
         // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
@@ -332,13 +368,11 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
 #pragma unroll
                     for (int q = 0; q < w; ++q) t[q] += t[q + w];
                 const double v = warp_sum(t[0]);
-                if (tid == 0) c.partials[slot * kMaxGrid + blockIdx.x] = v;
+                if (tid == 0) sync.publish(c, slot, v, &sh.cta_total);
             }
-            if (!grid_barrier(c, &sh.abort)) goto done;
+            if (!sync.barrier(c, &sh.abort)) goto done;
             if (tid < 32) {
-                double v = 0.0;
-                for (int i = tid; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
-                v = warp_sum(v);
+                const double v = sync.gather(c, slot, tid, &sh.cta_total);
                 if (tid == 0) {
                     // Eq. (Paccept) as dA < -log u (NaN compares false)
                     if (v < sh.elog[l]) {
@@ -360,7 +394,8 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
 
         // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
         const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
-        if (record) record_sample<Model, R>(c, n0, n1, blockIdx.x == 0, sh.p, sh.J == 0, tid, NT);
+        if (record)
+            record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
 
         // ---- step-size adaptation during burn-in (Sec. 4.2) ----
         if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
@@ -380,7 +415,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
         }
 
         // ---- parameter trace (for effective-sample-size diagnostics) ----
-        if (c.trace && blockIdx.x == 0 && tid < NP)
+        if (c.trace && sync.lead() && tid < NP)
             c.trace[(sh.tr_n % c.trace_cap) * NP + tid] = sh.p[tid];
 
         // ---- annealing, Eq. (fbeta): beta_{s+1} = beta_s f_beta until N_cool ----
@@ -409,13 +444,47 @@ done:
         atomicAdd(&g->site_prop[0], sh.site_prop[0]);
         atomicAdd(&g->site_prop[1], sh.site_prop[1]);
         atomicAdd(&g->nonfinite, sh.nonfinite);
-        if (blockIdx.x == 0) {
+        if (sync.lead()) {
             for (int l = 0; l < kMaxP; ++l) {
                 g->p[l] = sh.p[l]; g->sigp[l] = sh.sigp[l]; g->accp_win[l] = sh.accp_win[l];
                 g->par_acc[l] = sh.par_acc[l]; g->par_prop[l] = sh.par_prop[l];
             }
             g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx; g->tr_n = sh.tr_n;
         }
+    }
+    __syncthreads();
+}
+
+template <class Model, class R>
+__global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
+{
+    __shared__ SweepShared<R, kSweepBlock> sh;
+    const int64_t n0 = (int64_t)blockIdx.x * c.tile;
+    const int64_t n1 = min(n0 + c.tile, c.M + 1);
+    sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
+}
+
+// Many independent chains in one launch: CTA b runs, one after another, the
+// chains listed in order[first[b] .. first[b+1]) (whole chains, CTA-local
+// synchronisation, no inter-CTA waits).
+// FP32: at least 512 / NT resident CTAs per SM (at most 128 registers a thread).
+template <class R, int NT> struct BatchBounds { static constexpr int min_blocks = 1; };
+template <int NT> struct BatchBounds<float, NT> { static constexpr int min_blocks = 512 / NT; };
+
+template <class Model, class R, int NT>
+__global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
+    batch_sweep_kernel(const Ctx* chains, const int* first, const int* order, int64_t n_sweeps, uint64_t seed)
+{
+    __shared__ SweepShared<R, NT> sh;
+    __shared__ Ctx cs;  // the current chain's context, read from shared memory
+    for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
+        if (threadIdx.x == 0) {
+            cs = chains[order[i]];
+            cs.seed = seed;
+        }
+        __syncthreads();
+        sweep_chain<Model, R, NT>(cs, 0, cs.M + 1, n_sweeps, sh, BlockSync{});
+        __syncthreads();
     }
 }
 
@@ -461,6 +530,54 @@ int sweep_max_grid(int model, int prec, int device)
     if (model == 1) return max_grid_t<LinGauss<float>, float>(device);
     return max_grid_t<Toy1D<float>, float>(device);
 }
+
+// ---- batched launch --------------------------------------------------------
+
+template <class Model, class R, int NT>
+static cudaError_t batch_t(const Ctx* chains, const int* first, const int* order, int n_ctas, int64_t n_sweeps,
+                           uint64_t seed, cudaStream_t s)
+{
+    batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, 0, s>>>(chains, first, order, n_sweeps, seed);
+    return cudaGetLastError();
+}
+
+template <class Model, class R, int NT> static int batch_occ_t()
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<Model, R, NT>, NT, 0) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+#define PIMC_BATCH_DISPATCH(FN, ...)                                                               \
+    do {                                                                                           \
+        if (nt == 128) {                                                                           \
+            if (prec == 0) {                                                                       \
+                if (model == 0) return FN<HH<double>, double, 128>(__VA_ARGS__);                   \
+                if (model == 1) return FN<LinGauss<double>, double, 128>(__VA_ARGS__);             \
+                return FN<Toy1D<double>, double, 128>(__VA_ARGS__);                                \
+            }                                                                                      \
+            if (model == 0) return FN<HH<float>, float, 128>(__VA_ARGS__);                         \
+            if (model == 1) return FN<LinGauss<float>, float, 128>(__VA_ARGS__);                   \
+            return FN<Toy1D<float>, float, 128>(__VA_ARGS__);                                      \
+        }                                                                                          \
+        if (prec == 0) {                                                                           \
+            if (model == 0) return FN<HH<double>, double, 256>(__VA_ARGS__);                       \
+            if (model == 1) return FN<LinGauss<double>, double, 256>(__VA_ARGS__);                 \
+            return FN<Toy1D<double>, double, 256>(__VA_ARGS__);                                    \
+        }                                                                                          \
+        if (model == 0) return FN<HH<float>, float, 256>(__VA_ARGS__);                             \
+        if (model == 1) return FN<LinGauss<float>, float, 256>(__VA_ARGS__);                       \
+        return FN<Toy1D<float>, float, 256>(__VA_ARGS__);                                          \
+    } while (0)
+
+cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first, const int* order,
+                               int n_ctas, int64_t n_sweeps, uint64_t seed, cudaStream_t s)
+{
+    PIMC_BATCH_DISPATCH(batch_t, chains, first, order, n_ctas, n_sweeps, seed, s);
+}
+
+int batch_ctas_per_sm(int model, int prec, int nt) { PIMC_BATCH_DISPATCH(batch_occ_t); }
 
 // ---- diagnostic kernels sharing the sweep's per-site code ------------------
 

@@ -31,8 +31,10 @@ EXPORTS = [
     "pimc_set_chain", "pimc_sweep", "pimc_hmc", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
-    "pimc_launch_info", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
+    "pimc_launch_info", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
     "pimc_debug_skip_arrive", "pimc_set_grid", "pimc_action_static",
+    "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
+    "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
 ]
 
 
@@ -101,12 +103,21 @@ def _declare(L):
         "pimc_get_sweep": [_vp, _vp, _vp],
         "pimc_accept_stats": [_vp, _vp, _vp, _vp, _vp],
         "pimc_launch_info": [_vp, _vp, _vp],
+        "pimc_residual_moments": [_vp, _vp, _vp, _vp],
+        "pimc_forecast": [_vp, _i64, _vp, _int, _int, ctypes.c_uint64, _vp],
         "pimc_checkpoint_save": [_vp, ctypes.c_char_p],
         "pimc_checkpoint_load": [_vp, ctypes.c_char_p],
         "pimc_set_wait_limit": [_vp, _i64],
         "pimc_debug_skip_arrive": [_vp, _int],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+        "pimc_batch_create": [_vp, _vp, _int],
+        "pimc_batch_destroy": [_vp],
+        "pimc_batch_sweep": [_vp, _i64, ctypes.c_uint64],
+        "pimc_batch_sync": [_vp],
+        "pimc_batch_set_tuning": [_vp, _int, _int],
+        "pimc_batch_info": [_vp, _vp, _vp],
+        "pimc_batch_autotune": [_vp, _i64, ctypes.c_uint64, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -114,6 +125,8 @@ def _declare(L):
         f.restype = _int
     L.pimc_last_error.argtypes = [_vp]
     L.pimc_last_error.restype = ctypes.c_char_p
+    L.pimc_batch_last_error.argtypes = [_vp]
+    L.pimc_batch_last_error.restype = ctypes.c_char_p
 
 
 def _p(a):
@@ -273,6 +286,19 @@ class Sampler:
         self._ck(self._L.pimc_moments(self._h, _p(mean), _p(var), _p(J)))
         return mean, var, int(J[0])
 
+    def residual_moments(self):
+        nr = (self.D + 1) * self.M
+        mean, var = np.zeros(nr), np.zeros(nr)
+        J = np.zeros(1, dtype=np.int64)
+        self._ck(self._L.pimc_residual_moments(self._h, _p(mean), _p(var), _p(J)))
+        return mean, var, int(J[0])
+
+    def forecast(self, n_steps, I_future, n_ens, noise, seed):
+        out = np.zeros(int(n_ens) * self.D * (int(n_steps) + 1))
+        self._ck(self._L.pimc_forecast(self._h, int(n_steps), _p(_f64(I_future)), int(n_ens), int(noise),
+                                       int(seed), _p(out)))
+        return out.reshape(int(n_ens), self.D, int(n_steps) + 1)
+
     def set_histograms(self, comp, lo, hi, n_bins):
         comp = np.ascontiguousarray(comp, dtype=np.int64)
         self._ck(self._L.pimc_set_histograms(self._h, comp.size, _p(comp), _p(_f64(lo)), _p(_f64(hi)),
@@ -337,3 +363,53 @@ class Sampler:
 
     def checkpoint_load(self, path):
         self._ck(self._L.pimc_checkpoint_load(self._h, os.fsencode(path)))
+
+
+class Batch:
+    """Many chains (each a Sampler) in one launch; chain state stays in the Samplers."""
+
+    def __init__(self, samplers):
+        self._L = load()
+        self.samplers = list(samplers)
+        arr = (ctypes.c_void_p * len(self.samplers))(*[s._h.value for s in self.samplers])
+        b = ctypes.c_void_p()
+        r = self._L.pimc_batch_create(ctypes.byref(b), arr, len(self.samplers))
+        if r != OK:
+            raise PimcError(r, self._L.pimc_batch_last_error(None).decode())
+        self._b = b
+
+    def _ck(self, r):
+        if r != OK:
+            raise PimcError(r, self._L.pimc_batch_last_error(self._b).decode())
+
+    def sweep(self, n, seed, sync=True):
+        self._ck(self._L.pimc_batch_sweep(self._b, int(n), int(seed)))
+        if sync:
+            self.sync()
+
+    def sync(self):
+        self._ck(self._L.pimc_batch_sync(self._b))
+
+    def set_tuning(self, threads_per_cta, ctas_per_sm):
+        self._ck(self._L.pimc_batch_set_tuning(self._b, int(threads_per_cta), int(ctas_per_sm)))
+
+    def info(self):
+        n, t = ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.pimc_batch_info(self._b, ctypes.byref(n), ctypes.byref(t)))
+        return n.value, t.value
+
+    def autotune(self, trial_sweeps, seed):
+        t, k = ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.pimc_batch_autotune(self._b, int(trial_sweeps), int(seed), ctypes.byref(t), ctypes.byref(k)))
+        return t.value, k.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.pimc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

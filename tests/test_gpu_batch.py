@@ -1,0 +1,81 @@
+"""T-BATCH: many chains of uneven M in one batched launch.
+
+Each chain of a batch runs exactly the sweeps it runs alone on one CTA
+(pimc_set_grid(h, 1)): states, parameters and moments are bit-identical.
+Counters are keyed by the chain id, never by the CTA, so the assignment of
+chains to CTAs (the tiling, the autotuner's choice) does not change a chain.
+"""
+import numpy as np
+import pytest
+
+from paper_1103_4887_gb300 import pimc, synth
+
+pytestmark = pytest.mark.gpu
+
+MS = [37, 200, 511, 1000, 2500, 64, 1, 300]
+
+
+def _make(prec, grid1=False):
+    out = []
+    for k, M in enumerate(MS):
+        prob = synth.hh_problem(M, data_seed=100 + k, free="all" if k % 2 == 0 else ("gNa", "gK", "gL"))
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_chain(k)
+        s.set_schedule(n_init=12, n_skip=3, beta0=0.2, n_cool=8, f_acc=0.4, alpha=0.3)
+        if grid1:
+            s.set_grid(1)
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("prec", [pimc.FP64, pimc.FP32_MIXED])
+def test_batched_chains_equal_single_chain_runs_bitwise(prec):
+    alone = _make(prec, grid1=True)
+    for s in alone:
+        s.sweep(25, 77)
+    grouped = _make(prec)
+    b = pimc.Batch(grouped)
+    b.set_tuning(256, 0)
+    b.sweep(10, 77)
+    b.sweep(15, 77)   # a second graph (different length) continues the counters
+    for s1, s2 in zip(alone, grouped):
+        X1, p1 = s1.state()
+        X2, p2 = s2.state()
+        assert np.array_equal(X1, X2) and np.array_equal(p1, p2)
+        m1, v1, J1 = s1.moments()
+        m2, v2, J2 = s2.moments()
+        assert J1 == J2 and np.array_equal(m1, m2) and np.array_equal(v1, v2, equal_nan=True)
+        assert s1.sweep_counter() == s2.sweep_counter()
+        a1, a2 = s1.accept_stats(), s2.accept_stats()
+        for x, y in zip(a1, a2):
+            assert np.array_equal(x, y)
+
+
+def test_tiling_does_not_change_a_chain():
+    """128- and 256-thread CTAs, few or many chains per CTA: same chains (to
+    rounding of the CTA sum order)."""
+    ref = _make(pimc.FP64)
+    b = pimc.Batch(ref)
+    b.set_tuning(256, 1)
+    b.sweep(8, 5)
+    other = _make(pimc.FP64)
+    b2 = pimc.Batch(other)
+    b2.set_tuning(128, 0)
+    b2.sweep(8, 5)
+    for s1, s2 in zip(ref, other):
+        X1, p1 = s1.state()
+        X2, p2 = s2.state()
+        np.testing.assert_allclose(X2, X1, rtol=1e-11, atol=1e-11)
+        np.testing.assert_allclose(p2, p1, rtol=1e-11)
+
+
+def test_autotune_picks_a_valid_shape():
+    chains = _make(pimc.FP32_MIXED)
+    b = pimc.Batch(chains)
+    nt, k = b.autotune(3, 1)
+    assert nt in (128, 256) and k >= 1
+    n_ctas, t = b.info()
+    assert t == nt and 1 <= n_ctas <= len(chains)
+    b.sweep(5, 2)
+    for s in chains:
+        assert np.all(np.isfinite(s.state()[0]))

@@ -197,3 +197,34 @@ def test_T_CKPT_resume_is_bitwise(tmp_path):
         with pytest.raises(pimc.PimcError) as e:
             b.checkpoint_load(p)
         assert e.value.code == pimc.ERR_IO
+
+
+def test_residual_moments_and_forecast_parity():
+    prob = synth.hh_problem(120, data_seed=6, free="all")
+    g = pimc.Sampler.from_problem(prob)
+    g.set_schedule(n_init=3, n_skip=2)
+    eps, dl = [], []
+    for s in range(21):
+        g.sweep(1, 19)
+        if s >= 3 and (s - 3) % 2 == 0:
+            X, p = g.state()
+            f = np.array([oracle.model_map(0, prob.dt, X[:, n], p, prob.I[n]) for n in range(prob.M)]).T
+            eps.append((X[:, 1:] - f).ravel())
+            dl.append(X[0, 1:] - prob.y[1:])
+    R = np.hstack([np.array(eps), np.array(dl)])
+    mean, var, J = g.residual_moments()
+    assert J == R.shape[0] == 9
+    scale = np.abs(R).max(axis=0) + 1e-300
+    assert np.all(np.abs(mean - R.mean(0)) <= 1e-10 * scale)
+    np.testing.assert_allclose(var, R.var(0, ddof=1), rtol=1e-6, atol=1e-12 * scale.max() ** 2)
+    # ensemble forecast from the same state: oracle and GPU, with and without noise
+    X, p = g.state()
+    o = oracle.Chain(0, prob.M, prob.dt, prob.Rm, prob.Rf)
+    o.set_data(prob.y, prob.I)
+    o.set_params(p, prob.lo, prob.hi, prob.free)
+    o.set_path(X)
+    Ifut = synth.ou_current(50, prob.dt, 99)
+    for noise in (0, 1):
+        fg = g.forecast(50, Ifut, 64, noise, 5)
+        fo = o.forecast(50, Ifut, 64, noise, 5)
+        np.testing.assert_allclose(fg, fo, rtol=1e-10, atol=1e-10)

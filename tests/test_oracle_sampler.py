@@ -341,3 +341,43 @@ def test_hmc_closed_form_posterior():
     assert np.all(np.abs(tr.mean(0) - mu) < 4 * se)
     sq = (tr - mu) ** 2
     assert np.all(np.abs(sq.mean(0) - np.diag(cov)) < 4 * batch_se(sq))
+
+
+def test_residual_moments_match_numpy():
+    """Residual accumulators (eps_{n+1} = x_{n+1} - f(x_n), delta_n = x_{n,0} - y_n)
+    against numpy over the recorded samples, with f from the (pinned) map."""
+    prob = synth.hh_problem(25, data_seed=3)
+    ch = new_chain(prob)
+    ch.set_schedule(n_init=4, n_skip=2)
+    eps, dl = [], []
+    for s in range(30):
+        ch.sweep(1, 13)
+        if s >= 4 and (s - 4) % 2 == 0:
+            X, p = ch.state()
+            f = np.array([oracle.model_map(0, prob.dt, X[:, n], p, prob.I[n]) for n in range(prob.M)]).T
+            eps.append((X[:, 1:] - f).ravel())
+            dl.append(X[0, 1:] - prob.y[1:])
+    R = np.hstack([np.array(eps), np.array(dl)])
+    mean, var, J = ch.residual_moments()
+    assert J == R.shape[0] == 13
+    np.testing.assert_allclose(mean, R.mean(0), rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(var, R.var(0, ddof=1), rtol=1e-7, atol=1e-18)
+
+
+def test_forecast_deterministic_and_noise_law():
+    prob = synth.hh_problem(40, data_seed=1)
+    ch = new_chain(prob)
+    Ifut = 10.0 + np.zeros(25)
+    det = ch.forecast(25, Ifut, 3, 0, 1)
+    X, p = ch.state()
+    x = X[:, -1].copy()
+    for k in range(25):
+        assert np.array_equal(det[0, :, k], x)
+        x = oracle.model_map(0, prob.dt, x, p, Ifut[k])
+    assert np.array_equal(det[0], det[2])
+    # one noisy step: x_1 = f(x_0) + xi, xi_a ~ N(0, 1/Rf_a)
+    ens = ch.forecast(1, Ifut[:1], 20000, 1, 7)
+    d = ens[:, :, 1] - det[0, :, 1]
+    se = 1.0 / np.sqrt(prob.Rf) / np.sqrt(d.shape[0])
+    assert np.all(np.abs(d.mean(0)) < 4 * se)
+    assert np.all(np.abs(d.var(0) * prob.Rf - 1.0) < 4 * np.sqrt(2.0 / d.shape[0]))
