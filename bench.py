@@ -256,16 +256,22 @@ def run_batch(args):
     el = time.perf_counter() - t0
     sites = int(sum(int(m) + 1 for m in Ms)) * per_set
     n_ctas, _ = b.info()
-    print(json.dumps({"mode": "batch", "chains": n_sets * per_set, "data_sets": n_sets, "sites_per_sweep": sites,
-                      "sweeps": steps, "seconds": el, "site_updates_per_s": sites * steps / el,
-                      "ms_per_sweep_all_chains": 1e3 * el / steps, "tuning": {"threads_per_cta": nt,
-                      "ctas_per_sm": k, "ctas": n_ctas}, "precision": "fp32mixed"}), flush=True)
+    res = {"mode": "batch", "chains": n_sets * per_set, "data_sets": n_sets, "sites_per_sweep": sites,
+           "sweeps": steps, "seconds": el, "site_updates_per_s": sites * steps / el,
+           "ms_per_sweep_all_chains": 1e3 * el / steps, "tuning": {"threads_per_cta": nt,
+           "ctas_per_sm": k, "ctas": n_ctas}, "precision": "fp32mixed"}
+    b.close()
+    for s in samplers:
+        s.close()
+    return res
 
 
 def run_ess(args):
     """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
     all 7 parameters free): checkerboard Metropolis in FP32-mixed and FP64, and
-    whole-path HMC (FP64), each after an adaptive burn-in, on the same data."""
+    whole-path HMC (FP64), on the same data.  Chains start at the true path and
+    parameters and adapt during a burn-in, so the figure measures mixing in the
+    posterior, not the approach to it."""
     import torch
     from paper_1103_4887_gb300 import diagnostics, pimc, synth
     M = 16384
@@ -284,6 +290,8 @@ def run_ess(args):
     for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 20000),
                                 ("metropolis_fp64", pimc.FP64, 2000, 4000)):
         s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
+        s.set_path(prob.X_true)
         s.set_stream(st.cuda_stream)
         s.set_schedule(n_init=burn, n_skip=20, f_acc=0.4, alpha=0.5)
         s.sweep(burn, SEED, sync=False)
@@ -298,6 +306,8 @@ def run_ess(args):
 
     # whole-path HMC: diagonal mass from burn-in variances, step tuned to ~70 %
     s = pimc.Sampler.from_problem(prob, precision=pimc.FP64)
+    s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
+    s.set_path(prob.X_true)
     s.set_stream(st.cuda_stream)
     s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
     s.sweep(4000, SEED, sync=False)
@@ -318,7 +328,7 @@ def run_ess(args):
                        "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
                        "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
     s.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -330,6 +340,7 @@ def main():
     ap.add_argument("--precision", default="fp32mixed", choices=["fp32mixed", "fp64"])
     ap.add_argument("--M", type=int, default=M_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the batched and ESS measurements")
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
                     help="no timing: 3 single-sweep launches per precision (a small case for ncu)")
@@ -352,10 +363,10 @@ def main():
         run_sweep_M(args)
         return
     if args.ess:
-        run_ess(args)
+        print(json.dumps(run_ess(args)), flush=True)
         return
     if args.batch:
-        run_batch(args)
+        print(json.dumps(run_batch(args)), flush=True)
         return
 
     import torch
@@ -452,6 +463,7 @@ def main():
         fp64 = {"value": world * sites * args.fp64_steps / (sum(ms64) * 1e-3), "ms_per_step": sum(ms64) / len(ms64)}
         s64.close()
 
+    grid_block = list(samp.launch_info())
     peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -471,6 +483,19 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
+    extras = {}
+    if rank == 0 and world == 1 and not args.quick:
+        samp.close()
+        try:
+            extras["batch"] = run_batch(args)
+        except Exception as e:  # reported, not hidden
+            extras["batch"] = {"error": repr(e)}
+        try:
+            ess = run_ess(args)
+            extras["ess"] = {k: ({kk: v[kk] for kk in ("min_ess_per_s", "median_ess_per_s", "seconds")}
+                                 if isinstance(v, dict) else v) for k, v in ess.items()}
+        except Exception as e:
+            extras["ess"] = {"error": repr(e)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -479,10 +504,11 @@ def main():
                 "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": n_free,
                            "precision": args.precision, "sweeps_per_step": 1, "n_skip": NSKIP,
                            "l2": "flushed (256 MiB write) before every timed sweep",
-                           "grid_block": list(samp.launch_info())},
+                           "grid_block": grid_block},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk.rows),
                 "steady_state": steady, "fp64": fp64}
+        line.update(extras)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

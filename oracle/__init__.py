@@ -27,8 +27,10 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODEL_HH, MODEL_LINGAUSS, MODEL_TOY1D = 0, 1, 2
-MODEL_DIMS = {MODEL_HH: (4, 7), MODEL_LINGAUSS: (2, 1), MODEL_TOY1D: (1, 1)}
+MODEL_HH, MODEL_LINGAUSS, MODEL_TOY1D, MODEL_HH_PAPER = 0, 1, 2, 3
+MODEL_DIMS = {MODEL_HH: (4, 7), MODEL_LINGAUSS: (2, 1), MODEL_TOY1D: (1, 1), MODEL_HH_PAPER: (4, 7)}
+SCHEME_RK4, SCHEME_TRAPEZOID = 0, 1
+PROPOSAL_GAUSS, PROPOSAL_UNIFORM = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +77,9 @@ def _declare(L):
     L.orc_model_map.argtypes = [_int, _d, _vp, _vp, _d, _vp]
     L.orc_model_map_vjp.argtypes = [_int, _d, _vp, _vp, _d, _vp, _vp, _vp]
     L.orc_hh_rates.argtypes = [_d, _vp, _vp]
+    L.orc_paper_gates.argtypes = [_d, _vp, _vp]
+    L.orc_set_scheme.argtypes = [_vp, _int]
+    L.orc_set_proposal.argtypes = [_vp, _int]
     L.orc_create.argtypes = [_int, _i64, _d, _d, _vp]
     L.orc_create.restype = _vp
     L.orc_destroy.argtypes = [_vp]
@@ -184,6 +189,13 @@ def hh_rates(V):
     return a, b
 
 
+def paper_gates(V):
+    ainf = np.zeros(3)
+    tau = np.zeros(3)
+    lib().orc_paper_gates(float(V), _p(ainf), _p(tau))
+    return ainf, tau
+
+
 class Chain:
     """One Markov chain of the oracle sampler (serial FP64)."""
 
@@ -241,6 +253,14 @@ class Chain:
     def param_update(self, l, z, u):
         return int(lib().orc_param_update(self._h, int(l), float(z), float(u)))
 
+    def set_scheme(self, scheme):
+        if lib().orc_set_scheme(self._h, int(scheme)) != 0:
+            raise ValueError("bad scheme")
+
+    def set_proposal(self, kind):
+        if lib().orc_set_proposal(self._h, int(kind)) != 0:
+            raise ValueError("bad proposal kind")
+
     def set_chain(self, chain):
         lib().orc_set_chain(self._h, chain)
 
@@ -294,9 +314,9 @@ class Chain:
         return X.reshape(self.D, self.M + 1), p
 
     def cache(self):
-        f = np.zeros(self.D * self.M)
+        f = np.zeros(self.D * (self.M + 1))
         lib().orc_get_cache(self._h, _p(f))
-        return f.reshape(self.D, self.M)
+        return f.reshape(self.D, self.M + 1)
 
     def steps(self):
         sx = np.zeros(self.D * (self.M + 1))

@@ -131,6 +131,7 @@ int orc_model_dims(int model, int* D, int* Np)
     case ORC_MODEL_HH:       *D = 4; *Np = 7; return 0;
     case ORC_MODEL_LINGAUSS: *D = 2; *Np = 1; return 0;
     case ORC_MODEL_TOY1D:    *D = 1; *Np = 1; return 0;
+    case ORC_MODEL_HH_PAPER: *D = 4; *Np = 7; return 0;
     default: return -1;
     }
 }
@@ -176,6 +177,26 @@ static void orc_hh_rate_derivs(double V, double* dalpha, double* dbeta)
     dbeta[2]  = -b[2] / 80.0;
 }
 
+/* The paper's HH form (Sec. 5.1, Eq. (dVdt), Eq. (dadt)): gates relax to
+ * a_inf(V) = 1/2 + 1/2 tanh((V - V_a)/dV_a) with time constant
+ * tau_a(V) = tau_a0 + tau_a1 (1 - tanh^2((V - V_a)/dV_a)); constants of
+ * Table 1, here in the gate order m, h, n. */
+static const double ORC_TAB1[3][4] = {
+    /* V_a, dV_a, tau_a0, tau_a1 */
+    { 25.0, 15.0, 0.1, 0.4 },   /* m, Na activation */
+    { 5.0, -15.0, 1.0, 7.0 },   /* h, Na inactivation */
+    { 10.0, 30.0, 1.0, 5.0 },   /* n, K activation */
+};
+
+void orc_paper_gates(double V, double* ainf, double* tau)
+{
+    for (int g = 0; g < 3; ++g) {
+        double t = tanh((V - ORC_TAB1[g][0]) / ORC_TAB1[g][1]);
+        ainf[g] = 0.5 + 0.5 * t;
+        tau[g] = ORC_TAB1[g][2] + ORC_TAB1[g][3] * (1.0 - t * t);
+    }
+}
+
 /* Linear test model: dx/dt = K x + (p0, I), K a damped rotation. */
 static const double ORC_LG_K[2][2] = { { -0.5, -2.0 }, { 2.0, -0.5 } };
 
@@ -197,6 +218,14 @@ void orc_model_rhs(int model, const double* x, const double* p, double I, double
         F[1] = a[0] * (1.0 - m) - b[0] * m;
         F[2] = a[1] * (1.0 - h) - b[1] * h;
         F[3] = a[2] * (1.0 - n) - b[2] * n;
+    } else if (model == ORC_MODEL_HH_PAPER) {
+        /* dV/dt = p1 I + p2 m^3 h (p3 - V) + p4 n^4 (p5 - V) + p6 (p7 - V) */
+        double V = x[0], m = x[1], h = x[2], n = x[3];
+        double ainf[3], tau[3];
+        orc_paper_gates(V, ainf, tau);
+        F[0] = p[0] * I + p[1] * m * m * m * h * (p[2] - V) + p[3] * n * n * n * n * (p[4] - V)
+             + p[5] * (p[6] - V);
+        for (int g = 0; g < 3; ++g) F[1 + g] = (ainf[g] - x[1 + g]) / tau[g];
     } else if (model == ORC_MODEL_LINGAUSS) {
         F[0] = ORC_LG_K[0][0] * x[0] + ORC_LG_K[0][1] * x[1] + p[0];
         F[1] = ORC_LG_K[1][0] * x[0] + ORC_LG_K[1][1] * x[1] + I;
@@ -235,6 +264,30 @@ static void orc_model_rhs_vjp(int model, const double* x, const double* p, doubl
             double s = x[1 + g];
             gx[1 + g] += w[1 + g] * (-(a[g] + b[g]));
             gx[0] += w[1 + g] * (da[g] * (1.0 - s) - db[g] * s);
+        }
+    } else if (model == ORC_MODEL_HH_PAPER) {
+        double V = x[0], m = x[1], h = x[2], n = x[3];
+        double m3h = m * m * m * h, n4 = n * n * n * n;
+        gx[0] += w[0] * (-p[1] * m3h - p[3] * n4 - p[5]);
+        gx[1] += w[0] * (3.0 * p[1] * m * m * h * (p[2] - V));
+        gx[2] += w[0] * (p[1] * m * m * m * (p[2] - V));
+        gx[3] += w[0] * (4.0 * p[3] * n * n * n * (p[4] - V));
+        gp[0] += w[0] * I;
+        gp[1] += w[0] * (m3h * (p[2] - V));
+        gp[2] += w[0] * (p[1] * m3h);
+        gp[3] += w[0] * (n4 * (p[4] - V));
+        gp[4] += w[0] * (p[3] * n4);
+        gp[5] += w[0] * (p[6] - V);
+        gp[6] += w[0] * p[5];
+        for (int g = 0; g < 3; ++g) {
+            double t = tanh((V - ORC_TAB1[g][0]) / ORC_TAB1[g][1]);
+            double sech2 = 1.0 - t * t;
+            double ainf = 0.5 + 0.5 * t, tau = ORC_TAB1[g][2] + ORC_TAB1[g][3] * sech2;
+            double dainf = 0.5 * sech2 / ORC_TAB1[g][1];
+            double dtau = -2.0 * ORC_TAB1[g][3] * t * sech2 / ORC_TAB1[g][1];
+            double a = x[1 + g];
+            gx[1 + g] += w[1 + g] * (-1.0 / tau);
+            gx[0] += w[1 + g] * ((dainf * tau - (ainf - a) * dtau) / (tau * tau));
         }
     } else if (model == ORC_MODEL_LINGAUSS) {
         gx[0] += ORC_LG_K[0][0] * w[0] + ORC_LG_K[1][0] * w[1];
@@ -316,7 +369,9 @@ struct orc_state {
     double dt, Rm, Rf[ORC_MAXD];
     double *y, *I;             /* y[M+1], I[M] */
     double *X;                 /* D*(M+1) */
-    double *f;                 /* D*M: f(x_n) for n = 0..M-1 */
+    double *f;                 /* D*(M+1) cache g_n: RK4 map f(x_n) (n < M) or field F(x_n) (trapezoid, n <= M) */
+    int scheme;                /* ORC_SCHEME_RK4 or ORC_SCHEME_TRAPEZOID */
+    int proposal;              /* ORC_PROPOSAL_GAUSS or ORC_PROPOSAL_UNIFORM */
     double p[ORC_MAXP], lo[ORC_MAXP], hi[ORC_MAXP];
     uint8_t free_[ORC_MAXP];
     double xlo[ORC_MAXD], xhi[ORC_MAXD]; /* optional state box (default unbounded) */
@@ -342,21 +397,59 @@ struct orc_state {
 };
 
 #define XI(s, a, n) ((s)->X[(int64_t)(a) * ((s)->M + 1) + (n)])
-#define FI(s, a, n) ((s)->f[(int64_t)(a) * (s)->M + (n)])
+#define FI(s, a, n) ((s)->f[(int64_t)(a) * ((s)->M + 1) + (n)])
 
 static void orc_load_site(const orc_state* s, int64_t n, double* x)
 {
     for (int a = 0; a < s->D; ++a) x[a] = XI(s, a, n);
 }
 
+/* Number of cached sites: f(x_n) for n < M (RK4) or F(x_n) for n <= M (trapezoid). */
+static int64_t orc_cache_len(const orc_state* s) { return s->scheme == ORC_SCHEME_RK4 ? s->M : s->M + 1; }
+
+/* Drive at grid point n for the trapezoid rule: the held value of [t_n, t_{n+1}),
+ * and at t_M the last one. */
+static double orc_drive_at(const orc_state* s, int64_t n) { return n < s->M ? s->I[n] : s->I[s->M - 1]; }
+
+/* Cached value g_n of state x at site n for parameters p. */
+static void orc_cache_value(const orc_state* s, const double* x, const double* p, int64_t n, double* g)
+{
+    if (s->scheme == ORC_SCHEME_RK4) orc_model_map(s->model, s->dt, x, p, s->I[n], g);
+    else orc_model_rhs(s->model, x, p, orc_drive_at(s, n), g);
+}
+
+/* Model-error residual eps_{n+1} from x_n, x_{n+1} and their cached values:
+ * RK4: x_{n+1} - f(x_n); trapezoid (Eq. (modelError)):
+ * x_{n+1} - x_n - dt/2 [F(x_{n+1}) + F(x_n)]. */
+static double orc_eps(const orc_state* s, double xn, double xn1, double gn, double gn1)
+{
+    if (s->scheme == ORC_SCHEME_RK4) return xn1 - gn;
+    return xn1 - xn - 0.5 * s->dt * (gn1 + gn);
+}
+
 static void orc_refresh_cache(orc_state* s)
 {
-    double x[ORC_MAXD], fx[ORC_MAXD];
-    for (int64_t n = 0; n < s->M; ++n) {
+    double x[ORC_MAXD], g[ORC_MAXD];
+    for (int64_t n = 0; n < orc_cache_len(s); ++n) {
         orc_load_site(s, n, x);
-        orc_model_map(s->model, s->dt, x, s->p, s->I[n], fx);
-        for (int a = 0; a < s->D; ++a) FI(s, a, n) = fx[a];
+        orc_cache_value(s, x, s->p, n, g);
+        for (int a = 0; a < s->D; ++a) FI(s, a, n) = g[a];
     }
+}
+
+int orc_set_scheme(orc_state* s, int scheme)
+{
+    if (scheme != ORC_SCHEME_RK4 && scheme != ORC_SCHEME_TRAPEZOID) return -1;
+    s->scheme = scheme;
+    if (s->have_data && s->have_params) orc_refresh_cache(s);
+    return 0;
+}
+
+int orc_set_proposal(orc_state* s, int kind)
+{
+    if (kind != ORC_PROPOSAL_GAUSS && kind != ORC_PROPOSAL_UNIFORM) return -1;
+    s->proposal = kind;
+    return 0;
 }
 
 orc_state* orc_create(int model, int64_t M, double dt, double Rm, const double* Rf)
@@ -371,7 +464,7 @@ orc_state* orc_create(int model, int64_t M, double dt, double Rm, const double* 
     s->y = (double*)calloc((size_t)(M + 1), sizeof(double));
     s->I = (double*)calloc((size_t)M, sizeof(double));
     s->X = (double*)calloc((size_t)nc, sizeof(double));
-    s->f = (double*)calloc((size_t)(D * M), sizeof(double));
+    s->f = (double*)calloc((size_t)nc, sizeof(double));
     s->sig = (double*)calloc((size_t)nc, sizeof(double));
     s->acc_win = (uint32_t*)calloc((size_t)(M + 1), sizeof(uint32_t));
     s->site_margin = (double*)calloc((size_t)(M + 1), sizeof(double));
@@ -407,6 +500,10 @@ static void orc_default_path(orc_state* s)
             double a[3], b[3];
             orc_hh_rates(s->y[n], a, b);
             for (int g = 0; g < 3; ++g) XI(s, 1 + g, n) = a[g] / (a[g] + b[g]);
+        } else if (s->model == ORC_MODEL_HH_PAPER) {
+            double ainf[3], tau[3];
+            orc_paper_gates(s->y[n], ainf, tau);
+            for (int g = 0; g < 3; ++g) XI(s, 1 + g, n) = ainf[g];
         } else {
             for (int a = 1; a < s->D; ++a) XI(s, a, n) = 0.0;
         }
@@ -482,20 +579,22 @@ int orc_set_sweep_counter(orc_state* s, int64_t sweep, double beta)
 }
 
 /* ---- action ------------------------------------------------------------ */
-/* A_o = 1/2 sum_{n=1}^M Rm (x_{n,0} - y_n)^2;  A_f = 1/2 sum_{n=0}^{M-1} sum_a Rf_a eps_{n+1,a}^2,
- * eps_{n+1} = x_{n+1} - f(x_n, p; I_n)  (Sec. 2.1, with the explicit RK4 map). */
+/* A_o = 1/2 sum_{n=1}^M Rm (x_{n,0} - y_n)^2;  A_f = 1/2 sum_{n=0}^{M-1} sum_a Rf_a eps_{n+1,a}^2
+ * (Sec. 2.1), eps from the explicit RK4 map or the trapezoid rule. */
 void orc_action(const orc_state* s, double* A, double* Ao, double* Af)
 {
-    double ao = 0.0, af = 0.0, x[ORC_MAXD], fx[ORC_MAXD];
+    double ao = 0.0, af = 0.0, x[ORC_MAXD], x1[ORC_MAXD], g[ORC_MAXD], g1[ORC_MAXD];
     for (int64_t n = 1; n <= s->M; ++n) {
         double d = XI(s, 0, n) - s->y[n];
         ao += 0.5 * s->Rm * d * d;
     }
     for (int64_t n = 0; n < s->M; ++n) {
         orc_load_site(s, n, x);
-        orc_model_map(s->model, s->dt, x, s->p, s->I[n], fx);
+        orc_load_site(s, n + 1, x1);
+        orc_cache_value(s, x, s->p, n, g);
+        if (s->scheme == ORC_SCHEME_TRAPEZOID) orc_cache_value(s, x1, s->p, n + 1, g1);
         for (int a = 0; a < s->D; ++a) {
-            double e = XI(s, a, n + 1) - fx[a];
+            double e = orc_eps(s, x[a], x1[a], g[a], g1[a]);
             af += 0.5 * s->Rf[a] * e * e;
         }
     }
@@ -509,10 +608,10 @@ static double orc_sqdiff(double R, double dp, double d, double* scale)
     return 0.5 * R * (dp - d) * (dp + d);
 }
 
-/* Local change of action for replacing x_n by xp (Fig. 1 steps (c)-(g)):
- * measurement term at n (n >= 1), model-error terms eps_n (n >= 1, via the
- * cached f(x_{n-1})) and eps_{n+1} (n <= M-1, via fp = f(xp)). */
-static double orc_site_delta(const orc_state* s, int64_t n, const double* xp, const double* fp,
+/* Local change of action for replacing x_n by xp with cached value gp
+ * (Fig. 1 steps (c)-(g)): measurement term at n (n >= 1), model-error terms
+ * eps_n (n >= 1) and eps_{n+1} (n <= M-1) against the cached neighbours. */
+static double orc_site_delta(const orc_state* s, int64_t n, const double* xp, const double* gp,
                              double beta, double* scale)
 {
     double dA = 0.0, sc = 0.0;
@@ -521,8 +620,9 @@ static double orc_site_delta(const orc_state* s, int64_t n, const double* xp, co
         dA += orc_sqdiff(s->Rm, dp, d, &sc);
         double dAf = 0.0;
         for (int a = 0; a < s->D; ++a) {
-            double e = XI(s, a, n) - FI(s, a, n - 1);
-            double ep = xp[a] - FI(s, a, n - 1);
+            double gn = s->scheme == ORC_SCHEME_RK4 ? 0.0 : FI(s, a, n);
+            double e = orc_eps(s, XI(s, a, n - 1), XI(s, a, n), FI(s, a, n - 1), gn);
+            double ep = orc_eps(s, XI(s, a, n - 1), xp[a], FI(s, a, n - 1), s->scheme == ORC_SCHEME_RK4 ? 0.0 : gp[a]);
             double t = 0.0;
             dAf += orc_sqdiff(s->Rf[a], ep, e, &t);
             sc += beta * t;
@@ -532,8 +632,9 @@ static double orc_site_delta(const orc_state* s, int64_t n, const double* xp, co
     if (n <= s->M - 1) {
         double dAf = 0.0;
         for (int a = 0; a < s->D; ++a) {
-            double e = XI(s, a, n + 1) - FI(s, a, n);
-            double ep = XI(s, a, n + 1) - fp[a];
+            double g1 = s->scheme == ORC_SCHEME_RK4 ? 0.0 : FI(s, a, n + 1);
+            double e = orc_eps(s, XI(s, a, n), XI(s, a, n + 1), FI(s, a, n), g1);
+            double ep = orc_eps(s, xp[a], XI(s, a, n + 1), gp[a], g1);
             double t = 0.0;
             dAf += orc_sqdiff(s->Rf[a], ep, e, &t);
             sc += beta * t;
@@ -546,32 +647,40 @@ static double orc_site_delta(const orc_state* s, int64_t n, const double* xp, co
 
 void orc_site_delta_all(const orc_state* s, const double* Xp, double beta, double* dA, double* scale)
 {
-    double xp[ORC_MAXD], fp[ORC_MAXD];
+    double xp[ORC_MAXD], gp[ORC_MAXD] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t n = 0; n <= s->M; ++n) {
         for (int a = 0; a < s->D; ++a) xp[a] = Xp[(int64_t)a * (s->M + 1) + n];
-        if (n <= s->M - 1) orc_model_map(s->model, s->dt, xp, s->p, s->I[n], fp);
-        dA[n] = orc_site_delta(s, n, xp, fp, beta, scale ? &scale[n] : NULL);
+        if (n < orc_cache_len(s)) orc_cache_value(s, xp, s->p, n, gp);
+        dA[n] = orc_site_delta(s, n, xp, gp, beta, scale ? &scale[n] : NULL);
     }
 }
 
 /* Parameter move: the change of the model-error sum over the whole path when
- * p_l -> pl_new (Sec. 4.1, "Perturb parameter p_l" of Fig. 1), summed n = 0..M-1. */
+ * p -> pn (Sec. 4.1, "Perturb parameter p_l" of Fig. 1): new cached values
+ * for every site, then the sum over n = 0..M-1 of the residual changes. */
 static double orc_param_delta_cache(const orc_state* s, const double* pn, double beta,
-                                    double* fnew, double* scale)
+                                    double* gnew, double* scale)
 {
-    double x[ORC_MAXD], fp[ORC_MAXD], dA = 0.0, sc = 0.0;
-    for (int64_t n = 0; n < s->M; ++n) {
+    int64_t nc = orc_cache_len(s);
+    double* g = gnew ? gnew : (double*)malloc(sizeof(double) * (size_t)(s->D * (s->M + 1)));
+    double x[ORC_MAXD], gv[ORC_MAXD], dA = 0.0, sc = 0.0;
+    for (int64_t n = 0; n < nc; ++n) {
         orc_load_site(s, n, x);
-        orc_model_map(s->model, s->dt, x, pn, s->I[n], fp);
+        orc_cache_value(s, x, pn, n, gv);
+        for (int a = 0; a < s->D; ++a) g[(int64_t)a * (s->M + 1) + n] = gv[a];
+    }
+    for (int64_t n = 0; n < s->M; ++n) {
         for (int a = 0; a < s->D; ++a) {
-            double e = XI(s, a, n + 1) - FI(s, a, n);
-            double ep = XI(s, a, n + 1) - fp[a];
+            double g1o = s->scheme == ORC_SCHEME_RK4 ? 0.0 : FI(s, a, n + 1);
+            double g1n = s->scheme == ORC_SCHEME_RK4 ? 0.0 : g[(int64_t)a * (s->M + 1) + n + 1];
+            double e = orc_eps(s, XI(s, a, n), XI(s, a, n + 1), FI(s, a, n), g1o);
+            double ep = orc_eps(s, XI(s, a, n), XI(s, a, n + 1), g[(int64_t)a * (s->M + 1) + n], g1n);
             double t = 0.0;
             dA += beta * orc_sqdiff(s->Rf[a], ep, e, &t);
             sc += beta * t;
-            if (fnew) fnew[(int64_t)a * s->M + n] = fp[a];
         }
     }
+    if (!gnew) free(g);
     if (scale) *scale = sc;
     return dA;
 }
@@ -619,7 +728,8 @@ static void orc_record(orc_state* s)
      * delta_n = x_{n,0} - y_n */
     for (int64_t n = 0; n < s->M; ++n)
         for (int a = 0; a < s->D; ++a) {
-            double e = XI(s, a, n + 1) - FI(s, a, n);
+            double e = orc_eps(s, XI(s, a, n), XI(s, a, n + 1), FI(s, a, n),
+                               s->scheme == ORC_SCHEME_RK4 ? 0.0 : FI(s, a, n + 1));
             s->E1[(int64_t)a * s->M + n] += e;
             s->E2[(int64_t)a * s->M + n] += e * e;
         }
@@ -721,7 +831,7 @@ void orc_histograms(const orc_state* s, uint64_t* counts)
  * the store of x_n and its cached f_n. Returns 1 on accept. */
 int orc_site_update(orc_state* s, int64_t n, const double* z, double u)
 {
-    double x[ORC_MAXD], xp[ORC_MAXD], fp[ORC_MAXD], margin;
+    double x[ORC_MAXD], xp[ORC_MAXD], fp[ORC_MAXD] = {0.0, 0.0, 0.0, 0.0}, margin;
     int parity = (int)(n & 1);
     orc_load_site(s, n, x);
     int inside = 1;
@@ -732,24 +842,42 @@ int orc_site_update(orc_state* s, int64_t n, const double* z, double u)
     s->site_prop[parity] += 1;
     s->site_margin[n] = INFINITY;
     if (!inside) return 0;
-    if (n <= s->M - 1) orc_model_map(s->model, s->dt, xp, s->p, s->I[n], fp);
+    const int cached = n < orc_cache_len(s);
+    if (cached) orc_cache_value(s, xp, s->p, n, fp);
     double dA = orc_site_delta(s, n, xp, fp, s->beta, NULL);
     int acc = orc_accept(dA, u, &margin);
     s->site_margin[n] = margin;
     if (acc) {
         for (int a = 0; a < s->D; ++a) XI(s, a, n) = xp[a];
-        if (n <= s->M - 1) for (int a = 0; a < s->D; ++a) FI(s, a, n) = fp[a];
+        if (cached) for (int a = 0; a < s->D; ++a) FI(s, a, n) = fp[a];
         s->acc_win[n] += 1;
         s->site_acc[parity] += 1;
     }
     return acc;
 }
 
+/* Uniform proposal increments of Fig. 1, U(-1, 1) per component, from the same
+ * Philox words as the Gaussian ones: 2 u - 1 with u the open uniform of each
+ * word pair. */
+static void orc_site_uniform_draws(uint64_t seed, uint32_t chain, uint64_t sweep, int64_t n, int D, double* z,
+                                   double* u)
+{
+    uint32_t w[4];
+    for (int pair = 0; 2 * pair < D; ++pair) {
+        orc_block(seed, chain, sweep, (uint32_t)n, ORC_KIND_SITE, (uint32_t)pair, w);
+        z[2 * pair] = 2.0 * orc_u01(w[0], w[1]) - 1.0;
+        if (2 * pair + 1 < D) z[2 * pair + 1] = 2.0 * orc_u01(w[2], w[3]) - 1.0;
+    }
+    orc_block(seed, chain, sweep, (uint32_t)n, ORC_KIND_SITE, 2u, w);
+    *u = orc_u01(w[0], w[1]);
+}
+
 static void orc_site_phase(orc_state* s, int parity, uint64_t seed)
 {
     double z[ORC_MAXD], u;
     for (int64_t n = parity; n <= s->M; n += 2) {
-        orc_site_draws(seed, s->chain, (uint64_t)s->sweep, n, s->D, z, &u);
+        if (s->proposal == ORC_PROPOSAL_UNIFORM) orc_site_uniform_draws(seed, s->chain, (uint64_t)s->sweep, n, s->D, z, &u);
+        else orc_site_draws(seed, s->chain, (uint64_t)s->sweep, n, s->D, z, &u);
         orc_site_update(s, n, z, u);
     }
 }
@@ -769,13 +897,13 @@ int orc_param_update(orc_state* s, int l, double z, double u)
     double pn[ORC_MAXP];
     memcpy(pn, s->p, sizeof pn);
     pn[l] = pl;
-    double* fnew = (double*)malloc(sizeof(double) * (size_t)(s->D * s->M));
+    double* fnew = (double*)calloc((size_t)(s->D * (s->M + 1)), sizeof(double));
     double dA = orc_param_delta_cache(s, pn, s->beta, fnew, NULL);
     int acc = orc_accept(dA, u, &margin);
     s->par_margin[l] = margin;
     if (acc) {
         s->p[l] = pl;
-        memcpy(s->f, fnew, sizeof(double) * (size_t)(s->D * s->M));
+        memcpy(s->f, fnew, sizeof(double) * (size_t)(s->D * (s->M + 1)));
         s->accp_win[l] += 1;
         s->par_acc[l] += 1;
     }
@@ -790,6 +918,11 @@ static void orc_param_phase(orc_state* s, uint64_t seed)
         s->par_margin[l] = INFINITY;
         if (!s->free_[l]) continue;
         orc_param_draws(seed, s->chain, (uint64_t)s->sweep, l, &z, &u);
+        if (s->proposal == ORC_PROPOSAL_UNIFORM) {
+            uint32_t w[4];
+            orc_block(seed, s->chain, (uint64_t)s->sweep, (uint32_t)l, ORC_KIND_PARAM, 0u, w);
+            z = 2.0 * orc_u01(w[0], w[1]) - 1.0;
+        }
         orc_param_update(s, l, z, u);
     }
 }
@@ -842,6 +975,33 @@ void orc_grad(const orc_state* s, double beta, double* gX, double* gp)
     for (int l = 0; l < s->Np; ++l) gp[l] = 0.0;
     for (int64_t n = 1; n <= s->M; ++n)
         gX[n] += s->Rm * (XI(s, 0, n) - s->y[n]);
+    if (s->scheme == ORC_SCHEME_TRAPEZOID) {
+        /* eps_{n+1} = x_{n+1} - x_n - dt/2 [F(x_{n+1}) + F(x_n)], w = beta Rf . eps_{n+1}:
+         * dA/dx_{n+1} += w - dt/2 J(x_{n+1})^T w, dA/dx_n += -w - dt/2 J(x_n)^T w,
+         * dA/dp -= dt/2 [J_p(x_{n+1}) + J_p(x_n)]^T w */
+        double x1[ORC_MAXD], F0[ORC_MAXD], F1[ORC_MAXD], g0[ORC_MAXD], g1[ORC_MAXD];
+        for (int64_t n = 0; n < s->M; ++n) {
+            orc_load_site(s, n, x);
+            orc_load_site(s, n + 1, x1);
+            orc_model_rhs(s->model, x, s->p, orc_drive_at(s, n), F0);
+            orc_model_rhs(s->model, x1, s->p, orc_drive_at(s, n + 1), F1);
+            for (int a = 0; a < D; ++a) {
+                double e = x1[a] - x[a] - 0.5 * s->dt * (F1[a] + F0[a]);
+                w[a] = beta * s->Rf[a] * e;
+                g0[a] = 0.0;
+                g1[a] = 0.0;
+            }
+            for (int l = 0; l < s->Np; ++l) gpl[l] = 0.0;
+            orc_model_rhs_vjp(s->model, x, s->p, orc_drive_at(s, n), w, g0, gpl);
+            orc_model_rhs_vjp(s->model, x1, s->p, orc_drive_at(s, n + 1), w, g1, gpl);
+            for (int a = 0; a < D; ++a) {
+                gX[(int64_t)a * (s->M + 1) + n + 1] += w[a] - 0.5 * s->dt * g1[a];
+                gX[(int64_t)a * (s->M + 1) + n] += -w[a] - 0.5 * s->dt * g0[a];
+            }
+            for (int l = 0; l < s->Np; ++l) gp[l] -= 0.5 * s->dt * gpl[l];
+        }
+        return;
+    }
     for (int64_t n = 0; n < s->M; ++n) {
         orc_load_site(s, n, x);
         orc_model_map(s->model, s->dt, x, s->p, s->I[n], fx);
@@ -948,7 +1108,7 @@ void orc_get_state(const orc_state* s, double* X, double* p)
 
 void orc_get_cache(const orc_state* s, double* f)
 {
-    memcpy(f, s->f, sizeof(double) * (size_t)(s->D * s->M));
+    memcpy(f, s->f, sizeof(double) * (size_t)(s->D * (s->M + 1)));
 }
 
 void orc_get_steps(const orc_state* s, double* sig_x, double* sig_p)

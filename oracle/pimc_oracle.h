@@ -33,7 +33,12 @@
 extern "C" {
 #endif
 
-enum { ORC_MODEL_HH = 0, ORC_MODEL_LINGAUSS = 1, ORC_MODEL_TOY1D = 2 };
+enum { ORC_MODEL_HH = 0, ORC_MODEL_LINGAUSS = 1, ORC_MODEL_TOY1D = 2, ORC_MODEL_HH_PAPER = 3 };
+/* Model-error discretisation: explicit one-step RK4 map, or the trapezoid
+ * rule of Eq. (modelError) with the vector field cached per site. */
+enum { ORC_SCHEME_RK4 = 0, ORC_SCHEME_TRAPEZOID = 1 };
+/* Site/parameter proposal increments: N(0, 1) or U(-1, 1) (Fig. 1) times the step. */
+enum { ORC_PROPOSAL_GAUSS = 0, ORC_PROPOSAL_UNIFORM = 1 };
 
 typedef struct orc_state orc_state;
 
@@ -61,6 +66,8 @@ void orc_model_map_vjp(int model, double dt, const double* x, const double* p, d
                        const double* w, double* gx, double* gp);
 /* HH rate functions alpha/beta for gate g (0:m 1:h 2:n) at voltage V. */
 void orc_hh_rates(double V, double* alpha, double* beta);
+/* The paper's gate kinetics (Table 1): a_inf(V) and tau(V) for m, h, n. */
+void orc_paper_gates(double V, double* ainf, double* tau);
 
 /* ---- sampler state ---------------------------------------------------- */
 orc_state* orc_create(int model, int64_t M, double dt, double Rm, const double* Rf);
@@ -74,6 +81,8 @@ int  orc_set_schedule(orc_state* s, int64_t n_init, int64_t n_skip, double beta0
                       int64_t n_cool, double f_acc, double alpha);
 int  orc_set_chain(orc_state* s, uint32_t chain);
 int  orc_set_state_box(orc_state* s, const double* lo, const double* hi);
+int  orc_set_scheme(orc_state* s, int scheme);
+int  orc_set_proposal(orc_state* s, int kind);
 /* Single moves with explicit draws (the sweep calls these with Philox draws). */
 int  orc_site_update(orc_state* s, int64_t n, const double* z, double u);
 int  orc_param_update(orc_state* s, int l, double z, double u);

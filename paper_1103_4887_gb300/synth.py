@@ -116,6 +116,8 @@ class Problem:
     sig_p: np.ndarray        # (Np,)
     X_true: np.ndarray | None = None
     data_seed: int = 0
+    scheme: int = 0          # 0: explicit RK4 map, 1: trapezoid rule
+    proposal: int = 0        # 0: Gaussian, 1: uniform U(-1, 1) increments
 
     @property
     def D(self) -> int:
@@ -177,3 +179,68 @@ def toy_problem(M: int, data_seed: int = 0, dt: float = 0.1, Rm: float = 4.0, Rf
                    p_true=np.array([p0]), p_init=np.array([p0]), lo=np.array([lo]),
                    hi=np.array([hi]), free=np.array([1 if p_free else 0], dtype=np.uint8),
                    sig_x=np.array([0.4]), sig_p=np.array([0.3]), data_seed=data_seed)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own HH variant (Sec. 5.1): tanh gate kinetics with the Table 1
+# constants, the p1..p7 voltage equation in the shifted convention (rest near
+# 0 mV), 25 kHz sampling, R_d = diag(100, 1e6, 1e6, 1e6), R_o = 100.
+# ---------------------------------------------------------------------------
+PAPER_TRUTH = np.array([1.0, 120.0, 115.0, 20.0, -12.0, 0.3, 10.6])
+PAPER_NAMES = ("p1", "p2", "p3", "p4", "p5", "p6", "p7")
+_PAPER_GATES = np.array([[25.0, 15.0, 0.1, 0.4],     # m: V_a, dV_a, tau0, tau1
+                         [5.0, -15.0, 1.0, 7.0],     # h
+                         [10.0, 30.0, 1.0, 5.0]])    # n
+
+
+def _paper_field(s, q, I):
+    V, m, h, n = s
+    t = np.tanh((V - _PAPER_GATES[:, 0]) / _PAPER_GATES[:, 1])
+    ainf = 0.5 + 0.5 * t
+    tau = _PAPER_GATES[:, 2] + _PAPER_GATES[:, 3] * (1.0 - t * t)
+    dV = q[0] * I + q[1] * m ** 3 * h * (q[2] - V) + q[3] * n ** 4 * (q[4] - V) + q[5] * (q[6] - V)
+    return np.concatenate([[dV], (ainf - s[1:]) / tau])
+
+
+def paper_truth(M, dt, I, q=PAPER_TRUTH, substeps=10, relax_ms=50.0):
+    """Fine-grid integration of the paper's HH variant (drive held per interval)."""
+    h = dt / substeps
+    t = np.tanh((0.0 - _PAPER_GATES[:, 0]) / _PAPER_GATES[:, 1])
+    s = np.concatenate([[0.0], 0.5 + 0.5 * t])
+
+    def adv(s, I):
+        k1 = _paper_field(s, q, I)
+        k2 = _paper_field(s + 0.5 * h * k1, q, I)
+        k3 = _paper_field(s + 0.5 * h * k2, q, I)
+        k4 = _paper_field(s + h * k3, q, I)
+        return s + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+    for _ in range(int(relax_ms / h)):
+        s = adv(s, 0.0)
+    X = np.zeros((4, M + 1))
+    X[:, 0] = s
+    for n in range(M):
+        for _ in range(substeps):
+            s = adv(s, I[n])
+        X[:, n + 1] = s
+    return X
+
+
+def paper_problem(M, data_seed=0, free="all", dt=0.04, scheme=1, proposal=1, substeps=10):
+    """Problem in the paper's setting: HH variant, trapezoid rule, uniform proposals."""
+    q = PAPER_TRUTH.copy()
+    I = ou_current(M, dt, data_seed)
+    X = paper_truth(M, dt, I, q, substeps=substeps)
+    rng = np.random.default_rng([data_seed, 0xA9])
+    y = X[0] + 0.1 * rng.standard_normal(M + 1)
+    if free == "all":
+        free = PAPER_NAMES
+    fmask = np.array([1 if nm in free else 0 for nm in PAPER_NAMES], dtype=np.uint8)
+    u = np.random.default_rng([data_seed, 0x1A18]).uniform(-1.0, 1.0, 7)
+    p0 = np.where(fmask == 1, q * (1.0 + 0.2 * u), q)
+    lo = q - 0.5 * np.abs(q)
+    hi = q + 0.5 * np.abs(q)
+    return Problem(model=3, M=M, dt=dt, Rm=100.0, Rf=np.array([1e2, 1e6, 1e6, 1e6]), y=y, I=I,
+                   p_true=q, p_init=p0, lo=lo, hi=hi, free=fmask,
+                   sig_x=np.array([2e-3, 1e-3, 1e-3, 1e-3]), sig_p=0.002 * np.abs(p0), X_true=X,
+                   data_seed=data_seed, scheme=scheme, proposal=proposal)

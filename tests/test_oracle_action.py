@@ -17,6 +17,7 @@ from tests import _linear_gaussian as lgc
 
 def make_chain(prob, X=None):
     ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_scheme(prob.scheme)
     ch.set_data(prob.y, prob.I)
     ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
     if X is not None:
@@ -24,9 +25,11 @@ def make_chain(prob, X=None):
     return ch
 
 
-def test_lingauss_action_closed_form():
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_lingauss_action_closed_form(scheme):
     prob = synth.lingauss_problem(12, data_seed=3)
-    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
+    prob.scheme = scheme
+    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True, scheme=scheme)
     rng = np.random.default_rng(0)
     for _ in range(10):
         z = rng.standard_normal(L.shape[1])
@@ -41,9 +44,19 @@ def test_lingauss_action_closed_form():
         np.testing.assert_allclose(np.concatenate([gX.ravel(), gp]), g, rtol=1e-10, atol=1e-10)
 
 
+def _with_scheme(prob, scheme):
+    prob.scheme = scheme
+    return prob
+
+
 def _problems():
     hh = synth.hh_problem(40, data_seed=1, free="all")
-    return [("hh", hh), ("lg", synth.lingauss_problem(25, 2)), ("toy", synth.toy_problem(25, 4, p_free=True))]
+    return [("hh", hh), ("lg", synth.lingauss_problem(25, 2)), ("toy", synth.toy_problem(25, 4, p_free=True)),
+            ("paper_trap", synth.paper_problem(40, data_seed=2)),
+            ("paper_rk4", synth.paper_problem(40, data_seed=3, scheme=0)),
+            ("hh_trap", _with_scheme(synth.hh_problem(40, data_seed=4, free="all"), 1)),
+            ("lg_trap", _with_scheme(synth.lingauss_problem(25, 5), 1)),
+            ("toy_trap", _with_scheme(synth.toy_problem(25, 6, p_free=True), 1))]
 
 
 @pytest.mark.parametrize("name,prob", _problems())

@@ -103,11 +103,34 @@ def test_hh_rates_continuous_at_removable_singularities():
         assert max(abs(v - lim) for v in vals) < 1e-5 * lim + 1e-6
 
 
-@pytest.mark.parametrize("model", [HH, LG, TOY])
+def test_paper_variant_behaviour():
+    """The paper's HH variant (Sec. 5.1, Table 1) in the shifted convention:
+    a_inf(V_a) = 1/2 and tau(V_a) = tau0 + tau1 for each gate; the membrane
+    rests near 0 mV, and a 10 uA/cm^2 drive gives repeated overshooting spikes
+    ("qualitatively similar" to Hodgkin-Huxley)."""
+    for g, (Va, t0, t1) in enumerate([(25.0, 0.1, 0.4), (5.0, 1.0, 7.0), (10.0, 1.0, 5.0)]):
+        ainf, tau = oracle.paper_gates(Va)
+        assert ainf[g] == 0.5 and abs(tau[g] - (t0 + t1)) < 1e-15
+    p = np.array([1.0, 120.0, 115.0, 20.0, -12.0, 0.3, 10.6])
+    x = np.array([0.0, *oracle.paper_gates(0.0)[0]])
+    for _ in range(int(200 / 0.04)):
+        x = oracle.model_map(3, 0.04, x, p, 0.0)
+    assert abs(x[0]) < 2.0
+    assert np.max(np.abs(oracle.model_rhs(3, x, p, 0.0))) < 1e-9
+    V = []
+    for _ in range(int(300 / 0.04)):
+        x = oracle.model_map(3, 0.04, x, p, 10.0)
+        V.append(x[0])
+    V = np.array(V)
+    assert 90.0 < V.max() < 125.0
+    assert np.sum((V[1:] > 50) & (V[:-1] <= 50)) >= 8
+
+
+@pytest.mark.parametrize("model", [HH, LG, TOY, 3])
 def test_map_vjp_matches_central_differences(model):
     D, Np = oracle.MODEL_DIMS[model]
     rng = np.random.default_rng(11 + model)
-    dt = 0.02 if model == HH else 0.1
+    dt = 0.02 if model == HH else (0.04 if model == 3 else 0.1)
     for trial in range(6):
         if model == HH:
             x = np.array([rng.uniform(-80, 40), rng.uniform(0.05, 0.95),
@@ -115,6 +138,11 @@ def test_map_vjp_matches_central_differences(model):
             if trial == 0:
                 x[0] = -40.0 + 1e-5  # near the removable singularity of alpha_m
             p = P_HH * (1 + 0.1 * rng.uniform(-1, 1, 7))
+            I = rng.uniform(0, 20)
+        elif model == 3:
+            x = np.array([rng.uniform(-10, 100), rng.uniform(0.05, 0.95),
+                          rng.uniform(0.05, 0.95), rng.uniform(0.05, 0.95)])
+            p = np.array([1.0, 120.0, 115.0, 20.0, -12.0, 0.3, 10.6]) * (1 + 0.1 * rng.uniform(-1, 1, 7))
             I = rng.uniform(0, 20)
         else:
             x = rng.standard_normal(D)

@@ -21,6 +21,8 @@ from tests import _linear_gaussian as lgc
 
 def new_chain(prob, sig_x=None, sig_p=None):
     ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_scheme(prob.scheme)
+    ch.set_proposal(prob.proposal)
     ch.set_data(prob.y, prob.I)
     ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
     ch.set_steps(prob.sig_x if sig_x is None else sig_x, prob.sig_p if sig_p is None else sig_p)
@@ -381,3 +383,24 @@ def test_forecast_deterministic_and_noise_law():
     se = 1.0 / np.sqrt(prob.Rf) / np.sqrt(d.shape[0])
     assert np.all(np.abs(d.mean(0)) < 4 * se)
     assert np.all(np.abs(d.var(0) * prob.Rf - 1.0) < 4 * np.sqrt(2.0 / d.shape[0]))
+
+
+
+@pytest.mark.parametrize("scheme,proposal", [(1, 0), (1, 1), (0, 1)])
+def test_T_LG_trapezoid_and_uniform_proposals(scheme, proposal):
+    """The trapezoid rule of Eq. (modelError) keeps the linear model's posterior
+    Gaussian (closed form), and the uniform increments of Fig. 1 sample it too."""
+    prob = synth.lingauss_problem(**LG_ARGS)
+    prob.scheme, prob.proposal = scheme, proposal
+    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True, scheme=scheme)
+    mu, cov = lgc.posterior(L, r, w)
+    csd = 1.0 / np.sqrt(np.diag(np.linalg.inv(cov)))
+    nx = 2 * (prob.M + 1)
+    k = 1.0 if proposal == 0 else 1.7  # U(-1,1) has sd 1/sqrt(3)
+    ch = new_chain(prob, sig_x=k * csd[:nx].reshape(2, prob.M + 1), sig_p=np.array([2.0 * k * csd[-1]]))
+    ch.sweep(3000, 21)
+    tr = run_trace(ch, 150000, 21)
+    se = batch_se(tr)
+    assert np.all(np.abs(tr.mean(0) - mu) < 4 * se)
+    sq = (tr - mu) ** 2
+    assert np.all(np.abs(sq.mean(0) - np.diag(cov)) < 4 * batch_se(sq))
