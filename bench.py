@@ -266,6 +266,35 @@ def run_batch(args):
     return res
 
 
+def run_paper(args):
+    """The paper's Sec. 5.1 workload shape (M = 8000, D = 4, 7 free parameters,
+    trapezoid model error, tanh gate kinetics, uniform proposals) on synthetic
+    OU-driven data: device time per sweep and the time 10^6 sweeps would take,
+    beside the paper's 683 s for 10^6 sweeps on a GTX 460 in FP32 (context: other
+    hardware and other data)."""
+    import torch
+    from paper_1103_4887_gb300 import pimc, synth
+    prob = synth.paper_problem(8000, data_seed=0, free="all")
+    out = {"mode": "paper_setting", "M": 8000, "dt_ms": 0.04, "scheme": "trapezoid", "proposal": "uniform"}
+    st = torch.cuda.current_stream()
+    for name, prec, n in (("fp32mixed", pimc.FP32_MIXED, 2000), ("fp64", pimc.FP64, 200)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_stream(st.cuda_stream)
+        s.set_schedule(n_init=10 ** 9, n_skip=400)
+        s.sweep(20, SEED)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.sweep(n, SEED, sync=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        s.sync()
+        ms = e0.elapsed_time(e1) / n
+        out[name] = {"ms_per_sweep": ms, "site_updates_per_s": 8001 / (ms * 1e-3),
+                     "seconds_per_1e6_sweeps": ms * 1e3, "vs_paper_gtx460_683s": 683.0 / (ms * 1e3)}
+        s.close()
+    return out
+
+
 def run_ess(args):
     """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
     all 7 parameters free): checkerboard Metropolis in FP32-mixed and FP64, and
@@ -349,6 +378,9 @@ def main():
                          "and FP64, with the serial oracle timed on the host for the same M")
     ap.add_argument("--batch", action="store_true",
                     help="batched launch: 64 data sets (M ~ U[2048, 65536]) x 8 chains, FP32-mixed, autotuned")
+    ap.add_argument("--paper", action="store_true",
+                    help="the paper's own setting: HH variant with tanh kinetics, trapezoid rule, uniform "
+                         "proposals, M = 8000 at 25 kHz, all 7 parameters free")
     ap.add_argument("--ess", action="store_true",
                     help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
     args = ap.parse_args()
@@ -367,6 +399,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.paper:
+        print(json.dumps(run_paper(args)), flush=True)
         return
 
     import torch

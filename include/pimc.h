@@ -28,8 +28,8 @@
  *     enqueued; functions that return host data synchronise the stream and
  *     report any error flagged by a kernel (e.g. PIMC_ERR_TIMEOUT).
  *   * A handle is not thread-safe; separate handles are independent.
- *   * Sizes: M >= 1; D and N_p are fixed by the model (HH: D = 4, N_p = 7;
- *     LINGAUSS: D = 2, N_p = 1; TOY1D: D = 1, N_p = 1).
+ *   * Sizes: M >= 1; D and N_p are fixed by the model (HH and HH_PAPER: D = 4,
+ *     N_p = 7; LINGAUSS: D = 2, N_p = 1; TOY1D: D = 1, N_p = 1).
  */
 #ifndef PIMC_H
 #define PIMC_H
@@ -58,8 +58,22 @@ typedef enum {
     PIMC_MODEL_HH = 0,       /* Hodgkin-Huxley, x = (V, m, h, n),
                                 p = (gNa, gK, gL, ENa, EK, EL, C) (Sec. 5.1) */
     PIMC_MODEL_LINGAUSS = 1, /* dx/dt = K x + (p0, I), K = [[-0.5,-2],[2,-0.5]] (test model) */
-    PIMC_MODEL_TOY1D = 2     /* dx/dt = p0 sin(x) - x/2 + I (test model) */
+    PIMC_MODEL_TOY1D = 2,    /* dx/dt = p0 sin(x) - x/2 + I (test model) */
+    PIMC_MODEL_HH_PAPER = 3  /* the paper's HH form (Sec. 5.1, Eq. (dVdt), Eq. (dadt)):
+                                dV/dt = p1 I + p2 m^3 h (p3 - V) + p4 n^4 (p5 - V) + p6 (p7 - V),
+                                tanh gate kinetics with the Table 1 constants */
 } pimc_model;
+
+typedef enum {
+    PIMC_SCHEME_RK4 = 0,       /* eps_{n+1} = x_{n+1} - f(x_n), f one RK4 step (default) */
+    PIMC_SCHEME_TRAPEZOID = 1  /* eps_{n+1} = x_{n+1} - x_n - dt/2 [F(x_{n+1}) + F(x_n)],
+                                  Eq. (modelError); F cached per site (Sec. 4.3) */
+} pimc_scheme;
+
+typedef enum {
+    PIMC_PROPOSAL_GAUSS = 0,   /* x' = x + sigma . N(0, 1) (default) */
+    PIMC_PROPOSAL_UNIFORM = 1  /* x' = x + sigma . U(-1, 1), Fig. 1 step (a) */
+} pimc_proposal;
 
 typedef enum {
     PIMC_FP64 = 0,           /* every step in FP64 */
@@ -86,6 +100,13 @@ int pimc_set_stream(pimc_t h, void* stream);
 /* Select the arithmetic (pimc_precision).  Re-initialises the path from its
  * current FP64 value; call before pimc_sweep. */
 int pimc_set_precision(pimc_t h, int precision);
+
+/* Model-error discretisation (pimc_scheme).  With the trapezoid rule the
+ * vector field is evaluated at grid points; the drive there is I_inj[n] for
+ * n < M and I_inj[M-1] at t_M.  Refreshes the cache. */
+int pimc_set_scheme(pimc_t h, int scheme);
+/* Proposal increments of site and parameter moves (pimc_proposal). */
+int pimc_set_proposal(pimc_t h, int kind);
 
 /* ---- problem data (Sec. 4.1, "the current path, the observation time series,
  *      the external drive signal ... are allocated in GPU memory") ---------- */
@@ -207,7 +228,7 @@ int pimc_moments(pimc_t h, double* mean, double* var, int64_t* n_samples);
  * hold (D+1)*M doubles, eps_{n+1,a} = x_{n+1,a} - f_a(x_n) at [a*M + n]
  * (n = 0..M-1) and delta_n = x_{n,0} - y_n at [D*M + n - 1] (n = 1..M). */
 int pimc_residual_moments(pimc_t h, double* mean, double* var, int64_t* n_samples);
-/* Ensemble forecast from the current state (Sec. 6): n_ens members integrate
+/* Ensemble forecast from the current state (Sec. 6; explicit RK4 scheme only): n_ens members integrate
  * x_{k+1} = f(x_k, p; I_future[k]) + xi_k from x_M for n_steps steps, with
  * model noise xi_{k,a} ~ N(0, 1/Rf_a) when noise != 0 (none where Rf_a = 0);
  * normals are Philox draws keyed by (member, step, kind 4 | pair, chain).

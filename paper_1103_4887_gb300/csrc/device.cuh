@@ -53,6 +53,7 @@ __device__ __forceinline__ float u01f(uint32_t hi) { return ((float)(hi >> 8) + 
 template <class R> struct Num;
 
 template <> struct Num<double> {
+    static __device__ __forceinline__ double th(double x) { return tanh(x); }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
@@ -71,6 +72,13 @@ template <> struct Num<double> {
 };
 
 template <> struct Num<float> {
+    // SFU hyperbolic tangent (one MUFU.TANH instruction)
+    static __device__ __forceinline__ float th(float x)
+    {
+        float y;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     // SFU exponential (ex2.approx) and reciprocal for the per-site arithmetic
     static __device__ __forceinline__ float ex(float x) { return __expf(x); }
     static __device__ __forceinline__ float exm1(float x) { return __expf(x) - 1.0f; }
@@ -217,6 +225,80 @@ template <class R> struct HH {
     }
 };
 
+// The paper's HH form (Sec. 5.1, Eq. (dVdt) and Eq. (dadt)), shifted voltage
+// convention: dV/dt = p1 I + p2 m^3 h (p3 - V) + p4 n^4 (p5 - V) + p6 (p7 - V);
+// da/dt = (a_inf(V) - a)/tau_a(V), a_inf = 1/2 + 1/2 tanh((V - V_a)/dV_a),
+// tau_a = tau_a0 + tau_a1 (1 - tanh^2); Table 1 constants (gates m, h, n).
+template <class R> struct HHPaper {
+    static constexpr int D = 4, NP = 7;
+    static __device__ __forceinline__ void prep(const double* p, R* q)
+    {
+#pragma unroll
+        for (int l = 0; l < NP; ++l) q[l] = R(p[l]);
+        q[7] = R(0);
+    }
+    // V_a, 1/dV_a, tau_a0, tau_a1 of gate g (m, h, n)
+    static __device__ __forceinline__ void gate_const(int g, R& Va, R& idV, R& t0, R& t1)
+    {
+        if (g == 0) { Va = R(25); idV = R(1.0 / 15.0); t0 = R(0.1); t1 = R(0.4); }
+        else if (g == 1) { Va = R(5); idV = R(-1.0 / 15.0); t0 = R(1.0); t1 = R(7.0); }
+        else { Va = R(10); idV = R(1.0 / 30.0); t0 = R(1.0); t1 = R(5.0); }
+    }
+    static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F)
+    {
+        const R V = x[0], m = x[1], h = x[2], n = x[3];
+        F[0] = q[0] * I + q[1] * m * m * m * h * (q[2] - V) + q[3] * n * n * n * n * (q[4] - V) + q[5] * (q[6] - V);
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            R Va, idV, t0, t1;
+            gate_const(g, Va, idV, t0, t1);
+            const R t = Num<R>::th((V - Va) * idV);
+            const R ainf = R(0.5) + R(0.5) * t;
+            const R tau = t0 + t1 * (R(1) - t * t);
+            F[1 + g] = Num<R>::div(ainf - x[1 + g], tau);
+        }
+    }
+    static __device__ __forceinline__ void rhs_vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp)
+    {
+        const R V = x[0], m = x[1], h = x[2], n = x[3];
+        const R m3h = m * m * m * h, n4 = n * n * n * n;
+        gx[0] += w[0] * (-q[1] * m3h - q[3] * n4 - q[5]);
+        gx[1] += w[0] * (R(3) * q[1] * m * m * h * (q[2] - V));
+        gx[2] += w[0] * (q[1] * m * m * m * (q[2] - V));
+        gx[3] += w[0] * (R(4) * q[3] * n * n * n * (q[4] - V));
+        gp[0] += w[0] * I;
+        gp[1] += w[0] * (m3h * (q[2] - V));
+        gp[2] += w[0] * (q[1] * m3h);
+        gp[3] += w[0] * (n4 * (q[4] - V));
+        gp[4] += w[0] * (q[3] * n4);
+        gp[5] += w[0] * (q[6] - V);
+        gp[6] += w[0] * q[5];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            R Va, idV, t0, t1;
+            gate_const(g, Va, idV, t0, t1);
+            const R t = Num<R>::th((V - Va) * idV);
+            const R sech2 = R(1) - t * t;
+            const R ainf = R(0.5) + R(0.5) * t, tau = t0 + t1 * sech2;
+            const R dainf = R(0.5) * sech2 * idV;
+            const R dtau = R(-2) * t1 * t * sech2 * idV;
+            const R a = x[1 + g];
+            gx[1 + g] += w[1 + g] * (-R(1) / tau);
+            gx[0] += w[1 + g] * ((dainf * tau - (ainf - a) * dtau) / (tau * tau));
+        }
+    }
+    static __device__ __forceinline__ void init_site(R V, R* x)
+    {
+        x[0] = V;
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            R Va, idV, t0, t1;
+            gate_const(g, Va, idV, t0, t1);
+            x[1 + g] = R(0.5) + R(0.5) * Num<R>::th((V - Va) * idV);
+        }
+    }
+};
+
 // Linear test model: dx/dt = K x + (p0, I), K = [[-0.5, -2], [2, -0.5]].
 template <class R> struct LinGauss {
     static constexpr int D = 2, NP = 1;
@@ -256,6 +338,27 @@ template <class Model> struct ModelId;
 template <class R> struct ModelId<HH<R>> { static constexpr int value = 0; };
 template <class R> struct ModelId<LinGauss<R>> { static constexpr int value = 1; };
 template <class R> struct ModelId<Toy1D<R>> { static constexpr int value = 2; };
+template <class R> struct ModelId<HHPaper<R>> { static constexpr int value = 3; };
+
+// Model-error discretisations: the explicit one-step RK4 map, or the
+// trapezoid rule of Eq. (modelError) with the vector field cached per site.
+enum : int { kSchemeRK4 = 0, kSchemeTrapezoid = 1 };
+enum : int { kProposalGauss = 0, kProposalUniform = 1 };
+
+// Host-side dispatch of a template FN<Model, R> on (model, prec).
+#define PIMC_DISPATCH(FN, ...)                                                            \
+    do {                                                                                  \
+        if (prec == 0) {                                                                  \
+            if (model == 0) return FN<HH<double>, double>(__VA_ARGS__);                   \
+            if (model == 1) return FN<LinGauss<double>, double>(__VA_ARGS__);             \
+            if (model == 3) return FN<HHPaper<double>, double>(__VA_ARGS__);              \
+            return FN<Toy1D<double>, double>(__VA_ARGS__);                                \
+        }                                                                                 \
+        if (model == 0) return FN<HH<float>, float>(__VA_ARGS__);                         \
+        if (model == 1) return FN<LinGauss<float>, float>(__VA_ARGS__);                   \
+        if (model == 3) return FN<HHPaper<float>, float>(__VA_ARGS__);                    \
+        return FN<Toy1D<float>, float>(__VA_ARGS__);                                      \
+    } while (0)
 
 // One classical RK4 step of size dt with the drive held at I:
 // f = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).

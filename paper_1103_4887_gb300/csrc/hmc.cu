@@ -225,14 +225,7 @@ static cudaError_t hmc_traj_t(const Ctx& c, const HmcBuffers& b, int n_leap, dou
 cudaError_t launch_hmc_trajectory(int model, int prec, const Ctx& c, const HmcBuffers& b, int n_leap, double eps,
                                   uint64_t seed, cudaStream_t s)
 {
-    if (prec == 0) {
-        if (model == 0) return hmc_traj_t<HH<double>, double>(c, b, n_leap, eps, seed, s);
-        if (model == 1) return hmc_traj_t<LinGauss<double>, double>(c, b, n_leap, eps, seed, s);
-        return hmc_traj_t<Toy1D<double>, double>(c, b, n_leap, eps, seed, s);
-    }
-    if (model == 0) return hmc_traj_t<HH<float>, float>(c, b, n_leap, eps, seed, s);
-    if (model == 1) return hmc_traj_t<LinGauss<float>, float>(c, b, n_leap, eps, seed, s);
-    return hmc_traj_t<Toy1D<float>, float>(c, b, n_leap, eps, seed, s);
+    PIMC_DISPATCH(hmc_traj_t, c, b, n_leap, eps, seed, s);
 }
 
 }  // namespace pimc

@@ -34,9 +34,11 @@ constexpr int kStatusTimeout = 1;
 // Everything a kernel needs, passed by value.
 struct Ctx {
     int64_t M, ldx, ldf;          // sites 0..M; row strides of [D][ldx] and [D][ldf] arrays
+    int scheme;                   // kSchemeRK4 or kSchemeTrapezoid
+    int proposal;                 // kProposalGauss or kProposalUniform
     double dt, Rm, Rf[4];
     void* X;                      // R[D][ldx]
-    void* F[2];                   // R[D][ldf]: cached f(x_n), double-buffered (Sec. 4.3)
+    void* F[2];                   // R[D][ldf]: cached f(x_n) or F(x_n), double-buffered (Sec. 4.3)
     const void* y;                // R[ldx]
     const void* I;                // R[ldf]
     void* sig;                    // R[D][ldx]

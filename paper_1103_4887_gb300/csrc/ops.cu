@@ -3,6 +3,7 @@
 // through the RK4 map (stages recomputed), and path layout conversion.
 #include "device.cuh"
 #include "internal.h"
+#include "scheme.cuh"
 
 namespace pimc {
 
@@ -17,18 +18,19 @@ __global__ void init_path_kernel(Ctx c)
     for (int a = 0; a < D; ++a) ((R*)c.X)[a * c.ldx + n] = x[a];
 }
 
-// f_n = f(x_n, p; I_n) into the current cache buffer.
+// g_n = f(x_n, p; I_n) (RK4) or F(x_n, p; I_n) (trapezoid) into the current cache.
 template <class Model, class R>
 __global__ void refresh_cache_kernel(Ctx c)
 {
     constexpr int D = Model::D;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= c.M) return;
+    if (n >= cache_len(c)) return;
     R pr[kMaxP], x[D], f[D];
     Model::prep(c.st->p, pr);
+    const Coef<R> kc(c);
     const R* X = (const R*)c.X;
     for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
-    rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), f);
+    cache_value<Model, R>(c, kc, x, pr, n, f);
     R* F = (R*)c.F[c.st->fidx];
     for (int a = 0; a < D; ++a) F[a * c.ldf + n] = f[a];
 }
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(kBlock) action_kernel(Ctx c, const double* Xe,
     __shared__ double res[2];
     R pr[kMaxP];
     Model::prep(pe ? pe : c.st->p, pr);
+    const Coef<R> kc(c);
     double v[2] = {0.0, 0.0};
     const R* y = (const R*)c.y;
     for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n <= c.M; n += (int64_t)gridDim.x * kBlock) {
@@ -102,10 +105,12 @@ __global__ void __launch_bounds__(kBlock) action_kernel(Ctx c, const double* Xe,
             v[0] += 0.5 * c.Rm * (double)d * (double)d;
         }
         if (n < c.M) {
-            R f[D];
-            rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), f);
+            R g[D], g1[D], x1[D];
+            for (int a = 0; a < D; ++a) { x1[a] = path_at<R>(c, Xe, a, n + 1); g1[a] = R(0); }
+            cache_value<Model, R>(c, kc, x, pr, n, g);
+            if (c.scheme != kSchemeRK4) cache_value<Model, R>(c, kc, x1, pr, n + 1, g1);
             for (int a = 0; a < D; ++a) {
-                const R e = path_at<R>(c, Xe, a, n + 1) - f[a];
+                const R e = eps_of<R>(c, kc, x[a], x1[a], g[a], g1[a]);
                 v[1] += 0.5 * c.Rf[a] * (double)e * (double)e;
             }
         }
@@ -142,7 +147,26 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(Ctx c, const double* Xe, c
         double own[D];
         for (int a = 0; a < D; ++a) own[a] = 0.0;
         if (n >= 1) own[0] = c.Rm * (double)(x[0] - y[n]);
-        if (n < c.M) {
+        if (n < c.M && c.scheme != kSchemeRK4) {
+            // eps_{n+1} = x_{n+1} - x_n - dt/2 (F_{n+1} + F_n), w = beta Rf . eps:
+            // x_n gets -w - dt/2 J_n^T w, x_{n+1} gets w - dt/2 J_{n+1}^T w
+            const R* I = (const R*)c.I;
+            const R In = I[n], In1 = I[n + 1 < c.M ? n + 1 : c.M - 1];
+            R x1[D], F0[D], F1[D], w[D], g0[D], g1[D], gpl[kMaxP];
+            for (int a = 0; a < D; ++a) { x1[a] = path_at<R>(c, Xe, a, n + 1); g0[a] = R(0); g1[a] = R(0); }
+            for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
+            Model::rhs(x, pr, In, F0);
+            Model::rhs(x1, pr, In1, F1);
+            for (int a = 0; a < D; ++a)
+                w[a] = R(beta * c.Rf[a]) * (x1[a] - x[a] - R(0.5) * R(c.dt) * (F1[a] + F0[a]));
+            Model::rhs_vjp(x, pr, In, w, g0, gpl);
+            Model::rhs_vjp(x1, pr, In1, w, g1, gpl);
+            for (int a = 0; a < D; ++a) {
+                own[a] += -(double)w[a] - 0.5 * c.dt * (double)g0[a];
+                atomicAdd(&gX[a * ld + n + 1], (double)w[a] - 0.5 * c.dt * (double)g1[a]);
+            }
+            for (int l = 0; l < NP; ++l) vp[l] -= 0.5 * c.dt * (double)gpl[l];
+        } else if (n < c.M) {
             R w[D], f[D], fx[D], gpl[kMaxP];
             for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
             // f(x_n) first, for the residual that seeds the cotangent
@@ -260,17 +284,7 @@ static cudaError_t grad_t(const Ctx& c, const double* Xe, const double* pe, doub
     return cudaGetLastError();
 }
 
-#define PIMC_DISPATCH(FN, ...)                                                            \
-    do {                                                                                  \
-        if (prec == 0) {                                                                  \
-            if (model == 0) return FN<HH<double>, double>(__VA_ARGS__);                   \
-            if (model == 1) return FN<LinGauss<double>, double>(__VA_ARGS__);             \
-            return FN<Toy1D<double>, double>(__VA_ARGS__);                                \
-        }                                                                                 \
-        if (model == 0) return FN<HH<float>, float>(__VA_ARGS__);                         \
-        if (model == 1) return FN<LinGauss<float>, float>(__VA_ARGS__);                   \
-        return FN<Toy1D<float>, float>(__VA_ARGS__);                                      \
-    } while (0)
+
 
 cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s) { PIMC_DISPATCH(init_t, c, s); }
 cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s)

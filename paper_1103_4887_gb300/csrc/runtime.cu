@@ -19,6 +19,7 @@ using namespace pimc;
 
 struct pimc_handle_s {
     int model = 0, D = 0, NP = 0, prec = 0;
+    int scheme = 0, proposal = 0;
     int64_t M = 0, ldx = 0, ldf = 0;
     double dt = 0, Rm = 0, Rf[4] = {0, 0, 0, 0};
     int device = 0, num_sms = 0;
@@ -99,6 +100,7 @@ Ctx make_ctx(pimc_t h)
 {
     Ctx c{};
     c.M = h->M; c.ldx = h->ldx; c.ldf = h->ldf;
+    c.scheme = h->scheme; c.proposal = h->proposal;
     c.dt = h->dt; c.Rm = h->Rm;
     for (int a = 0; a < 4; ++a) c.Rf[a] = h->Rf[a];
     c.X = h->X; c.F[0] = h->F[0]; c.F[1] = h->F[1]; c.y = h->y; c.I = h->I; c.sig = h->sig;
@@ -254,6 +256,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
     case PIMC_MODEL_HH: Dm = 4; NP = 7; break;
     case PIMC_MODEL_LINGAUSS: Dm = 2; NP = 1; break;
     case PIMC_MODEL_TOY1D: Dm = 1; NP = 1; break;
+    case PIMC_MODEL_HH_PAPER: Dm = 4; NP = 7; break;
     default: return fail(nullptr, PIMC_ERR_ARG, "unknown model %d", model);
     }
     if (M < 1 || M > (int64_t)1 << 31) return fail(nullptr, PIMC_ERR_ARG, "M must be in [1, 2^31], got %lld", (long long)M);
@@ -269,7 +272,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
     h->model = model; h->D = D; h->NP = NP; h->M = M; h->dt = dt; h->Rm = *Rm;
     for (int a = 0; a < D; ++a) h->Rf[a] = Rf[a];
     h->ldx = round_up(M + 1, 64);
-    h->ldf = round_up(M, 64);
+    h->ldf = round_up(M + 1, 64);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -378,6 +381,24 @@ int pimc_set_precision(pimc_t h, int precision)
     if (h->have_data && (r = convert_data(h)) != PIMC_OK) return r;
     choose_grid(h);
     return refresh(h);
+}
+
+int pimc_set_scheme(pimc_t h, int scheme)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (scheme != PIMC_SCHEME_RK4 && scheme != PIMC_SCHEME_TRAPEZOID) return fail(h, PIMC_ERR_ARG, "unknown scheme %d", scheme);
+    h->scheme = scheme;
+    h->ctx_version++;
+    return refresh(h);
+}
+
+int pimc_set_proposal(pimc_t h, int kind)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (kind != PIMC_PROPOSAL_GAUSS && kind != PIMC_PROPOSAL_UNIFORM) return fail(h, PIMC_ERR_ARG, "unknown proposal %d", kind);
+    h->proposal = kind;
+    h->ctx_version++;
+    return PIMC_OK;
 }
 
 int pimc_set_data(pimc_t h, const double* y, const double* I_inj)
@@ -647,6 +668,7 @@ int pimc_forecast(pimc_t h, int64_t n_steps, const double* I_future, int n_ens, 
     if (!h->have_data || !h->have_params) return fail(h, PIMC_ERR_STATE, "pimc_forecast before data/params");
     if (n_steps < 0 || n_ens < 1 || !out || (n_steps > 0 && !I_future))
         return fail(h, PIMC_ERR_ARG, "bad forecast arguments");
+    if (h->scheme != PIMC_SCHEME_RK4) return fail(h, PIMC_ERR_STATE, "forecasts integrate the explicit RK4 map (scheme RK4)");
     if (!check_finite(I_future, n_steps)) return fail(h, PIMC_ERR_ARG, "I_future has non-finite values");
     const size_t nout = (size_t)n_ens * h->D * (n_steps + 1);
     double *dI = nullptr, *dout = nullptr;
@@ -947,7 +969,7 @@ struct Reader {
 };
 
 const char kMagic[8] = {'P', 'I', 'M', 'C', 'C', 'K', 'P', 'T'};
-const uint32_t kVersion = 2;
+const uint32_t kVersion = 3;
 
 }  // namespace
 
@@ -957,11 +979,11 @@ extern "C" int pimc_checkpoint_save(pimc_t h, const char* path)
     int r = pull_state(h);
     if (r != PIMC_OK) return r;
     const int64_t n1 = h->M + 1, nd = (int64_t)h->D * n1, nc = nd + h->NP;
-    std::vector<double> X(nd), S(nd), F0((size_t)(h->D * h->M)), F1((size_t)(h->D * h->M)), S1(nc), S2(nc), SH(nc);
+    std::vector<double> X(nd), S(nd), F0((size_t)nd), F1((size_t)nd), S1(nc), S2(nc), SH(nc);
     if ((r = get_rows(h, X.data(), h->X, h->ldx, n1)) != PIMC_OK) return r;
     if ((r = get_rows(h, S.data(), h->sig, h->ldx, n1)) != PIMC_OK) return r;
-    if ((r = get_rows(h, F0.data(), h->F[0], h->ldf, h->M)) != PIMC_OK) return r;
-    if ((r = get_rows(h, F1.data(), h->F[1], h->ldf, h->M)) != PIMC_OK) return r;
+    if ((r = get_rows(h, F0.data(), h->F[0], h->ldf, n1)) != PIMC_OK) return r;
+    if ((r = get_rows(h, F1.data(), h->F[1], h->ldf, n1)) != PIMC_OK) return r;
     std::vector<uint32_t> acc((size_t)n1);
     CK(h, cudaMemcpy(acc.data(), h->acc_win, sizeof(uint32_t) * n1, cudaMemcpyDeviceToHost));
     CK(h, cudaMemcpy(S1.data(), h->S1, sizeof(double) * nc, cudaMemcpyDeviceToHost));
@@ -978,7 +1000,7 @@ extern "C" int pimc_checkpoint_save(pimc_t h, const char* path)
         CK(h, cudaMemcpy(hh.data(), h->h_hi, sizeof(double) * h->n_sel, cudaMemcpyDeviceToHost));
     }
     Writer w;
-    w.val(h->model); w.val(h->prec); w.val(h->M); w.val(h->D); w.val(h->NP);
+    w.val(h->model); w.val(h->prec); w.val(h->M); w.val(h->D); w.val(h->NP); w.val(h->scheme); w.val(h->proposal);
     w.val(h->dt); w.val(h->Rm); w.put(h->Rf, sizeof h->Rf);
     w.val(h->n_init); w.val(h->n_skip); w.val(h->n_cool);
     w.val(h->beta0); w.val(h->fbeta); w.val(h->f_acc); w.val(h->alpha); w.val(h->chain);
@@ -1040,20 +1062,21 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
     if (!ok) return fail(h, PIMC_ERR_IO, "%s: not a checkpoint of this version, or truncated", path);
     if (crc32(buf.data(), buf.size()) != crc) return fail(h, PIMC_ERR_IO, "%s: CRC mismatch", path);
     Reader rd{buf.data(), buf.size()};
-    int model, prec, D, NP;
+    int model, prec, D, NP, scheme, proposal;
     int64_t M;
     double dt, Rm, Rf[4];
-    ok = rd.val(model) && rd.val(prec) && rd.val(M) && rd.val(D) && rd.val(NP) && rd.val(dt) && rd.val(Rm) &&
-         rd.get(Rf, sizeof Rf);
+    ok = rd.val(model) && rd.val(prec) && rd.val(M) && rd.val(D) && rd.val(NP) && rd.val(scheme) &&
+         rd.val(proposal) && rd.val(dt) && rd.val(Rm) && rd.get(Rf, sizeof Rf);
     if (!ok || model != h->model || M != h->M || D != h->D || NP != h->NP)
         return fail(h, PIMC_ERR_IO, "%s: checkpoint of a different problem shape", path);
     h->dt = dt; h->Rm = Rm;
+    h->scheme = scheme; h->proposal = proposal;
     memcpy(h->Rf, Rf, sizeof Rf);
     DevState hs{};
     ok = rd.val(h->n_init) && rd.val(h->n_skip) && rd.val(h->n_cool) && rd.val(h->beta0) && rd.val(h->fbeta) &&
          rd.val(h->f_acc) && rd.val(h->alpha) && rd.val(h->chain) && rd.val(hs);
     const int64_t n1 = M + 1, nd = (int64_t)D * n1, nc = nd + NP;
-    std::vector<double> y(n1), I(M), X(nd), S(nd), F0((size_t)(D * M)), F1((size_t)(D * M)), S1(nc), S2(nc), SH(nc);
+    std::vector<double> y(n1), I(M), X(nd), S(nd), F0((size_t)nd), F1((size_t)nd), S1(nc), S2(nc), SH(nc);
     std::vector<uint32_t> acc(n1);
     ok = ok && rd.get(y.data(), sizeof(double) * n1) && rd.get(I.data(), sizeof(double) * M) &&
          rd.get(X.data(), sizeof(double) * nd) && rd.get(S.data(), sizeof(double) * nd) &&
@@ -1085,17 +1108,17 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
     h->have_params = true;
     if ((r = put_rows(h, h->X, X.data())) != PIMC_OK) return r;
     if ((r = put_rows(h, h->sig, S.data())) != PIMC_OK) return r;
-    // cache rows are [D][M] with stride ldf
+    // cache rows are [D][M+1] with stride ldf
     {
         const size_t es = esize(h);
-        std::vector<unsigned char> t((size_t)D * M * es);
+        std::vector<unsigned char> t((size_t)D * n1 * es);
         for (int b = 0; b < 2; ++b) {
             const std::vector<double>& src = b == 0 ? F0 : F1;
             for (size_t i = 0; i < src.size(); ++i) {
                 if (prec == PIMC_FP64) memcpy(&t[i * es], &src[i], es);
                 else { float v = (float)src[i]; memcpy(&t[i * es], &v, es); }
             }
-            CK(h, cudaMemcpy2D(h->F[b], es * h->ldf, t.data(), es * M, es * M, D, cudaMemcpyHostToDevice));
+            CK(h, cudaMemcpy2D(h->F[b], es * h->ldf, t.data(), es * n1, es * n1, D, cudaMemcpyHostToDevice));
         }
     }
     CK(h, cudaMemcpy(h->acc_win, acc.data(), sizeof(uint32_t) * n1, cudaMemcpyHostToDevice));

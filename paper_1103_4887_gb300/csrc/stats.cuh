@@ -6,6 +6,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "scheme.cuh"
 
 namespace pimc {
 
@@ -28,8 +29,8 @@ __device__ __forceinline__ void accumulate(const Ctx& c, int64_t ci, double v, b
 }
 
 // Thread t of nt records its share; p is the current parameter vector and Fc
-// the current f cache (f(x_n) for n < M), which gives the model-error
-// residuals eps_{n+1} = x_{n+1} - f(x_n) without another map evaluation; the
+// the current cache (f(x_n) or F(x_n)), which gives the model-error residuals
+// eps_{n+1} without another map evaluation; the
 // measurement residuals are delta_n = x_{n,0} - y_n (their statistics are the
 // model check of Sec. 6).
 template <class Model, class R>
@@ -43,9 +44,12 @@ __device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_
 #pragma unroll
         for (int a = 0; a < D; ++a) accumulate(c, (int64_t)a * (M + 1) + n, (double)X[a * c.ldx + n], first_rec);
         if (n < M) {
+            const bool trap = c.scheme != kSchemeRK4;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const double e = (double)X[a * c.ldx + n + 1] - (double)Fc[a * c.ldf + n];
+                const double xn = (double)X[a * c.ldx + n], xn1 = (double)X[a * c.ldx + n + 1];
+                const double gn = (double)Fc[a * c.ldf + n];
+                const double e = trap ? xn1 - xn - 0.5 * c.dt * ((double)Fc[a * c.ldf + n + 1] + gn) : xn1 - gn;
                 c.R1[(int64_t)a * M + n] += e;
                 c.R2[(int64_t)a * M + n] += e * e;
             }

@@ -11,22 +11,10 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "scheme.cuh"
 #include "stats.cuh"
 
 namespace pimc {
-
-// Scalar constants of the action in the arithmetic type, formed once per
-// kernel so the per-site code does no FP64 -> FP32 conversions.
-template <class R> struct Coef {
-    R dt, Rm, Rf[kMaxD];
-    __device__ __forceinline__ explicit Coef(const Ctx& c)
-    {
-        dt = R(c.dt);
-        Rm = R(c.Rm);
-#pragma unroll
-        for (int a = 0; a < kMaxD; ++a) Rf[a] = R(c.Rf[a]);
-    }
-};
 
 template <class R, int NT> struct SweepShared {
     double p[kMaxP], lo[kMaxP], hi[kMaxP], sigp[kMaxP];
@@ -40,6 +28,7 @@ template <class R, int NT> struct SweepShared {
     R q_cur[kMaxP];                   // current model parameters in R
     R q_new[kMaxP][kMaxP];            // proposed vector for each parameter move, in R
     R tpart[NT];                    // per-thread partial sums of a parameter move
+    R halo[kMaxD];                  // trapezoid: F(x_{n1}, p') of the next tile's first site
     double cta_total;               // CTA sum of a parameter move (CTA-local chains)
     int abort;
     unsigned long long site_acc[2], site_prop[2], nonfinite;
@@ -92,12 +81,9 @@ __device__ bool grid_barrier(const Ctx& c, int* s_abort)
     return !*s_abort;
 }
 
-// Local change of action for x_n -> xp (Fig. 1 steps (c)-(g)): the
-// measurement term at n (n >= 1), the model-error term eps_n against the
-// cached f(x_{n-1}) (n >= 1) and eps_{n+1} against f(xp) (n <= M-1).
-// Nb holds the neighbourhood values loaded before the map is evaluated.
+// Neighbourhood of site n loaded before its map is evaluated.
 template <class R, int D> struct Nbhd {
-    R yn, fprev[D], xn1[D], fcur[D];
+    R yn, xprev[D], gprev[D], gcur[D], xn1[D], gn1[D];
 };
 
 template <class Model, class R>
@@ -105,23 +91,32 @@ __device__ __forceinline__ void load_nbhd(const Ctx& c, int64_t n, const R* Fc, 
 {
     constexpr int D = Model::D;
     const R* X = (const R*)c.X;
+    const bool trap = c.scheme != kSchemeRK4;
     if (n >= 1) {
         nb.yn = ((const R*)c.y)[n];
 #pragma unroll
-        for (int a = 0; a < D; ++a) nb.fprev[a] = Fc[a * c.ldf + n - 1];
+        for (int a = 0; a < D; ++a) {
+            nb.gprev[a] = Fc[a * c.ldf + n - 1];
+            nb.xprev[a] = trap ? X[a * c.ldx + n - 1] : R(0);
+        }
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a) nb.gcur[a] = (n < cache_len(c)) ? Fc[a * c.ldf + n] : R(0);
     if (n < c.M) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             nb.xn1[a] = X[a * c.ldx + n + 1];
-            nb.fcur[a] = Fc[a * c.ldf + n];
+            nb.gn1[a] = trap ? Fc[a * c.ldf + n + 1] : R(0);
         }
     }
 }
 
+// Local change of action for x_n -> xp with cached value gp (Fig. 1 steps
+// (c)-(g)): the measurement term at n (n >= 1) and the model-error terms
+// eps_n (n >= 1) and eps_{n+1} (n <= M-1), each as 1/2 R (e' - e)(e' + e).
 template <class Model, class R>
 __device__ __forceinline__ R site_delta(const Ctx& c, const Coef<R>& k, int64_t n, const R* x, const R* xp,
-                                        const R* fp, R beta, const Nbhd<R, Model::D>& nb)
+                                        const R* gp, R beta, const Nbhd<R, Model::D>& nb)
 {
     constexpr int D = Model::D;
     R dA = R(0);
@@ -129,20 +124,29 @@ __device__ __forceinline__ R site_delta(const Ctx& c, const Coef<R>& k, int64_t 
         dA += sqdiff<R>(k.Rm, xp[0] - nb.yn, x[0] - nb.yn);
         R dAf = R(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) dAf += sqdiff<R>(k.Rf[a], xp[a] - nb.fprev[a], x[a] - nb.fprev[a]);
+        for (int a = 0; a < D; ++a) {
+            const R e = eps_of<R>(c, k, nb.xprev[a], x[a], nb.gprev[a], nb.gcur[a]);
+            const R ep = eps_of<R>(c, k, nb.xprev[a], xp[a], nb.gprev[a], gp[a]);
+            dAf += sqdiff<R>(k.Rf[a], ep, e);
+        }
         dA += beta * dAf;
     }
     if (n < c.M) {
         R dAf = R(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) dAf += sqdiff<R>(k.Rf[a], nb.xn1[a] - fp[a], nb.xn1[a] - nb.fcur[a]);
+        for (int a = 0; a < D; ++a) {
+            const R e = eps_of<R>(c, k, x[a], nb.xn1[a], nb.gcur[a], nb.gn1[a]);
+            const R ep = eps_of<R>(c, k, xp[a], nb.xn1[a], gp[a], nb.gn1[a]);
+            dAf += sqdiff<R>(k.Rf[a], ep, e);
+        }
         dA += beta * dAf;
     }
     return dA;
 }
 
-// Proposal normals of site n at sweep s: D Box-Muller normals (cos then sin
-// per pair of blocks 0, 1) and the accept uniform (block 2).
+// Proposal increments of site n at sweep s: D Box-Muller normals (cos then
+// sin per pair of blocks 0, 1) or U(-1, 1) from the same words, and the
+// accept uniform (block 2).
 template <class Model, class R>
 __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n, R* z, R& u)
 {
@@ -150,7 +154,13 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
 #pragma unroll
     for (int pair = 0; 2 * pair < D; ++pair) {
         R z0, z1;
-        Num<R>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)n, kKindSite, pair), z0, z1);
+        const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)n, kKindSite, pair);
+        if (c.proposal == kProposalUniform) {
+            z0 = R(2) * Num<R>::uni(w.x, w.y) - R(1);
+            z1 = R(2) * Num<R>::uni(w.z, w.w) - R(1);
+        } else {
+            Num<R>::box_muller(w, z0, z1);
+        }
         z[2 * pair] = z0;
         if (2 * pair + 1 < D) z[2 * pair + 1] = z1;
     }
@@ -158,8 +168,8 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
     u = Num<R>::uni(w.x, w.y);
 }
 
-// One site move: proposal, f(x'), Delta A_n, Metropolis (as dA < -log u,
-// Eq. (Paccept)), store on accept.
+// One site move: proposal, its cached value, Delta A_n, Metropolis (as
+// dA < -log u, Eq. (Paccept)), store on accept.
 template <class Model, class R>
 __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
                                           R beta, R* Fc, unsigned long long& nonfinite)
@@ -167,7 +177,7 @@ __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_
     constexpr int D = Model::D;
     R* X = (R*)c.X;
     const R* sig = (const R*)c.sig;
-    R x[D], xp[D], fp[D], z[D], u;
+    R x[D], xp[D], gp[D], z[D], u;
     Nbhd<R, D> nb;
 #pragma unroll
     for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
@@ -176,25 +186,29 @@ __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_
     const R E = neglog<R>(u);
 #pragma unroll
     for (int a = 0; a < D; ++a) xp[a] = x[a] + sig[a * c.ldx + n] * z[a];
-    const bool has_next = n < c.M;
-    if (has_next) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], k.dt, fp);
-    const R dA = site_delta<Model, R>(c, k, n, x, xp, fp, beta, nb);
+    const bool cached = n < cache_len(c);
+    if (cached) cache_value<Model, R>(c, k, xp, pr, n, gp);
+    else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gp[a] = R(0);
+    }
+    const R dA = site_delta<Model, R>(c, k, n, x, xp, gp, beta, nb);
     if (!isfinite(dA)) ++nonfinite;
     const bool acc = dA < E;
     if (acc) {
 #pragma unroll
         for (int a = 0; a < D; ++a) X[a * c.ldx + n] = xp[a];
-        if (has_next) {
+        if (cached) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) Fc[a * c.ldf + n] = fp[a];
+            for (int a = 0; a < D; ++a) Fc[a * c.ldf + n] = gp[a];
         }
         c.acc_win[n] += 1u;
     }
     return acc;
 }
 
-// Site n's share of a parameter move: f(x_n, p') into the inactive cache and
-// beta/2 sum_a Rf_a [(x_{n+1} - f')^2 - (x_{n+1} - f)^2].
+// RK4 scheme: site n's share of a parameter move -- f(x_n, p') into the
+// inactive cache and beta/2 sum_a Rf_a [(x_{n+1} - f')^2 - (x_{n+1} - f)^2].
 template <class Model, class R>
 __device__ __forceinline__ R param_term(const Ctx& c, const Coef<R>& k, int64_t n, const R* pq, R beta,
                                         const R* Fc, R* Fn)
@@ -214,6 +228,41 @@ __device__ __forceinline__ R param_term(const Ctx& c, const Coef<R>& k, int64_t 
     for (int a = 0; a < D; ++a) {
         Fn[a * c.ldf + n] = fp[a];
         t += beta * sqdiff<R>(k.Rf[a], xn1[a] - fp[a], xn1[a] - fc[a]);
+    }
+    return t;
+}
+
+// Trapezoid scheme, first pass: F(x_n, p') of site n into the inactive cache.
+template <class Model, class R>
+__device__ __forceinline__ void trap_field(const Ctx& c, const Coef<R>& k, int64_t n, const R* pq, R* Fn, R* g)
+{
+    constexpr int D = Model::D;
+    const R* X = (const R*)c.X;
+    R x[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    cache_value<Model, R>(c, k, x, pq, n, g);
+    if (Fn) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = g[a];
+    }
+}
+
+// Trapezoid scheme, second pass: the change of eps_{n+1} when F_n, F_{n+1}
+// become F'_n, F'_{n+1} (gn1p: the new field at n+1).
+template <class Model, class R>
+__device__ __forceinline__ R trap_term(const Ctx& c, const Coef<R>& k, int64_t n, R beta, const R* Fc, const R* Fn,
+                                       const R* gn1p)
+{
+    constexpr int D = Model::D;
+    const R* X = (const R*)c.X;
+    R t = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const R xn = X[a * c.ldx + n], xn1 = X[a * c.ldx + n + 1];
+        const R e = eps_of<R>(c, k, xn, xn1, Fc[a * c.ldf + n], Fc[a * c.ldf + n + 1]);
+        const R ep = eps_of<R>(c, k, xn, xn1, Fn[a * c.ldf + n], gn1p[a]);
+        t += beta * sqdiff<R>(k.Rf[a], ep, e);
     }
     return t;
 }
@@ -312,7 +361,9 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
             const int l = tid - (NT - 32);
             if ((sh.free_mask >> l) & 1u) {
                 double z0, z1;
-                Num<double>::box_muller(draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u), z0, z1);
+                const uint4 wz = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u);
+                if (c.proposal == kProposalUniform) z0 = 2.0 * u01d(wz.x, wz.y) - 1.0;
+                else Num<double>::box_muller(wz, z0, z1);
                 const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
                 const double pl = sh.p[l] + sh.sigp[l] * z0;
                 sh.pnew[l] = pl;
@@ -354,7 +405,26 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
             R* Fn = (R*)c.F[sh.fidx ^ 1u];
             R part = R(0);
             const int64_t nend = min(n1, M);
-            for (int64_t n = n0 + tid; n < nend; n += NT) part += param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn);
+            if (c.scheme == kSchemeRK4) {
+                for (int64_t n = n0 + tid; n < nend; n += NT) part += param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn);
+            } else {
+                // trapezoid: F(x_n, p') of the tile (and of the next tile's
+                // first site, recomputed here), then the residual changes
+                R g[D];
+                for (int64_t n = n0 + tid; n < n1; n += NT) trap_field<Model, R>(c, kc, n, pq, Fn, g);
+                if (n1 <= M && tid == NT - 1) {
+                    trap_field<Model, R>(c, kc, n1, pq, nullptr, g);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) sh.halo[a] = g[a];
+                }
+                __syncthreads();
+                for (int64_t n = n0 + tid; n < nend; n += NT) {
+                    R gn1p[D];
+#pragma unroll
+                    for (int a = 0; a < D; ++a) gn1p[a] = (n + 1 < n1) ? Fn[a * c.ldf + n + 1] : sh.halo[a];
+                    part += trap_term<Model, R>(c, kc, n, beta, Fc, Fn, gn1p);
+                }
+            }
             // CTA sum in FP64 from the per-thread partials up, by one warp (pairwise within a lane)
             sh.tpart[tid] = part;
             __syncthreads();
@@ -509,26 +579,12 @@ static int max_grid_t(int device)
 
 cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s)
 {
-    if (prec == 0) {
-        if (model == 0) return launch_sweep_t<HH<double>, double>(c, n_sweeps, grid, s);
-        if (model == 1) return launch_sweep_t<LinGauss<double>, double>(c, n_sweeps, grid, s);
-        return launch_sweep_t<Toy1D<double>, double>(c, n_sweeps, grid, s);
-    }
-    if (model == 0) return launch_sweep_t<HH<float>, float>(c, n_sweeps, grid, s);
-    if (model == 1) return launch_sweep_t<LinGauss<float>, float>(c, n_sweeps, grid, s);
-    return launch_sweep_t<Toy1D<float>, float>(c, n_sweeps, grid, s);
+    PIMC_DISPATCH(launch_sweep_t, c, n_sweeps, grid, s);
 }
 
 int sweep_max_grid(int model, int prec, int device)
 {
-    if (prec == 0) {
-        if (model == 0) return max_grid_t<HH<double>, double>(device);
-        if (model == 1) return max_grid_t<LinGauss<double>, double>(device);
-        return max_grid_t<Toy1D<double>, double>(device);
-    }
-    if (model == 0) return max_grid_t<HH<float>, float>(device);
-    if (model == 1) return max_grid_t<LinGauss<float>, float>(device);
-    return max_grid_t<Toy1D<float>, float>(device);
+    PIMC_DISPATCH(max_grid_t, device);
 }
 
 // ---- batched launch --------------------------------------------------------
@@ -555,19 +611,23 @@ template <class Model, class R, int NT> static int batch_occ_t()
             if (prec == 0) {                                                                       \
                 if (model == 0) return FN<HH<double>, double, 128>(__VA_ARGS__);                   \
                 if (model == 1) return FN<LinGauss<double>, double, 128>(__VA_ARGS__);             \
+                if (model == 3) return FN<HHPaper<double>, double, 128>(__VA_ARGS__);              \
                 return FN<Toy1D<double>, double, 128>(__VA_ARGS__);                                \
             }                                                                                      \
             if (model == 0) return FN<HH<float>, float, 128>(__VA_ARGS__);                         \
             if (model == 1) return FN<LinGauss<float>, float, 128>(__VA_ARGS__);                   \
+            if (model == 3) return FN<HHPaper<float>, float, 128>(__VA_ARGS__);                    \
             return FN<Toy1D<float>, float, 128>(__VA_ARGS__);                                      \
         }                                                                                          \
         if (prec == 0) {                                                                           \
             if (model == 0) return FN<HH<double>, double, 256>(__VA_ARGS__);                       \
             if (model == 1) return FN<LinGauss<double>, double, 256>(__VA_ARGS__);                 \
+            if (model == 3) return FN<HHPaper<double>, double, 256>(__VA_ARGS__);                  \
             return FN<Toy1D<double>, double, 256>(__VA_ARGS__);                                    \
         }                                                                                          \
         if (model == 0) return FN<HH<float>, float, 256>(__VA_ARGS__);                             \
         if (model == 1) return FN<LinGauss<float>, float, 256>(__VA_ARGS__);                       \
+        if (model == 3) return FN<HHPaper<float>, float, 256>(__VA_ARGS__);                        \
         return FN<Toy1D<float>, float, 256>(__VA_ARGS__);                                          \
     } while (0)
 
@@ -599,12 +659,15 @@ __global__ void __launch_bounds__(kBlock) site_delta_kernel(Ctx c, const double*
         xp[a] = R(Xp[a * (c.M + 1) + n]);
     }
     load_nbhd<Model, R>(c, n, Fc, nb);
-    if (n < c.M) rk4_map<Model, R>(xp, pr, ((const R*)c.I)[n], kc.dt, fp);
+    for (int a = 0; a < D; ++a) fp[a] = R(0);
+    if (n < cache_len(c)) cache_value<Model, R>(c, kc, xp, pr, n, fp);
     dA[n] = (double)site_delta<Model, R>(c, kc, n, x, xp, fp, R(beta), nb);
 }
 
 // Full-path parameter change of action: per-CTA sums in FP64, then the last
-// CTA to finish adds them in CTA order (single pass, deterministic).
+// CTA to finish adds them in CTA order (single pass, deterministic).  For the
+// trapezoid rule the new field of every site is written first
+// (trap_field_kernel) and read by this kernel.
 template <class Model, class R>
 __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, double pl_new, double beta, double* out)
 {
@@ -619,8 +682,15 @@ __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, doubl
     Model::prep(pd, pq);
     const Coef<R> kc(c);
     R part = R(0);
-    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < c.M; n += (int64_t)gridDim.x * kBlock)
-        part += param_term<Model, R>(c, kc, n, pq, R(beta), Fc, Fn);
+    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < c.M; n += (int64_t)gridDim.x * kBlock) {
+        if (c.scheme == kSchemeRK4) {
+            part += param_term<Model, R>(c, kc, n, pq, R(beta), Fc, Fn);
+        } else {
+            R gn1p[Model::D];
+            for (int a = 0; a < Model::D; ++a) gn1p[a] = Fn[a * c.ldf + n + 1];
+            part += trap_term<Model, R>(c, kc, n, R(beta), Fc, Fn, gn1p);
+        }
+    }
     const double bs = block_sum<kBlock>((double)part, wsum);
     if (threadIdx.x == 0) {
         c.red[blockIdx.x] = bs;
@@ -638,6 +708,20 @@ __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, doubl
 }
 
 template <class Model, class R>
+__global__ void trap_field_kernel(Ctx c, int l, double pl_new)
+{
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > c.M) return;
+    double pd[kMaxP];
+    for (int q = 0; q < kMaxP; ++q) pd[q] = c.st->p[q];
+    pd[l] = pl_new;
+    R pq[kMaxP], g[Model::D];
+    Model::prep(pd, pq);
+    const Coef<R> kc(c);
+    trap_field<Model, R>(c, kc, n, pq, (R*)c.F[c.st->fidx ^ 1u], g);
+}
+
+template <class Model, class R>
 static cudaError_t site_delta_t(const Ctx& c, const double* Xp, double beta, double* dA, cudaStream_t s)
 {
     const int grid = (int)((c.M + 1 + kBlock - 1) / kBlock);
@@ -648,6 +732,11 @@ static cudaError_t site_delta_t(const Ctx& c, const double* Xp, double beta, dou
 template <class Model, class R>
 static cudaError_t param_delta_t(const Ctx& c, int l, double pl, double beta, double* out, cudaStream_t s)
 {
+    if (c.scheme != kSchemeRK4) {
+        trap_field_kernel<Model, R><<<(unsigned)((c.M + 1 + 255) / 256), 256, 0, s>>>(c, l, pl);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     int grid = (int)((c.M + kBlock - 1) / kBlock);
     if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid < 1) grid = 1;
@@ -658,27 +747,13 @@ static cudaError_t param_delta_t(const Ctx& c, int l, double pl, double beta, do
 cudaError_t launch_site_delta(int model, int prec, const Ctx& c, const double* Xp, double beta, double* dA,
                               cudaStream_t s)
 {
-    if (prec == 0) {
-        if (model == 0) return site_delta_t<HH<double>, double>(c, Xp, beta, dA, s);
-        if (model == 1) return site_delta_t<LinGauss<double>, double>(c, Xp, beta, dA, s);
-        return site_delta_t<Toy1D<double>, double>(c, Xp, beta, dA, s);
-    }
-    if (model == 0) return site_delta_t<HH<float>, float>(c, Xp, beta, dA, s);
-    if (model == 1) return site_delta_t<LinGauss<float>, float>(c, Xp, beta, dA, s);
-    return site_delta_t<Toy1D<float>, float>(c, Xp, beta, dA, s);
+    PIMC_DISPATCH(site_delta_t, c, Xp, beta, dA, s);
 }
 
 cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double pl_new, double beta,
                                double* out, cudaStream_t s)
 {
-    if (prec == 0) {
-        if (model == 0) return param_delta_t<HH<double>, double>(c, l, pl_new, beta, out, s);
-        if (model == 1) return param_delta_t<LinGauss<double>, double>(c, l, pl_new, beta, out, s);
-        return param_delta_t<Toy1D<double>, double>(c, l, pl_new, beta, out, s);
-    }
-    if (model == 0) return param_delta_t<HH<float>, float>(c, l, pl_new, beta, out, s);
-    if (model == 1) return param_delta_t<LinGauss<float>, float>(c, l, pl_new, beta, out, s);
-    return param_delta_t<Toy1D<float>, float>(c, l, pl_new, beta, out, s);
+    PIMC_DISPATCH(param_delta_t, c, l, pl_new, beta, out, s);
 }
 
 }  // namespace pimc

@@ -16,8 +16,10 @@ import numpy as np
 from . import build as _build
 
 FP64, FP32_MIXED = 0, 1
-MODEL_HH, MODEL_LINGAUSS, MODEL_TOY1D = 0, 1, 2
-MODEL_DIMS = {MODEL_HH: (4, 7), MODEL_LINGAUSS: (2, 1), MODEL_TOY1D: (1, 1)}
+MODEL_HH, MODEL_LINGAUSS, MODEL_TOY1D, MODEL_HH_PAPER = 0, 1, 2, 3
+MODEL_DIMS = {MODEL_HH: (4, 7), MODEL_LINGAUSS: (2, 1), MODEL_TOY1D: (1, 1), MODEL_HH_PAPER: (4, 7)}
+SCHEME_RK4, SCHEME_TRAPEZOID = 0, 1
+PROPOSAL_GAUSS, PROPOSAL_UNIFORM = 0, 1
 
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NUMERIC, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
 _ERRNAMES = {ERR_ARG: "PIMC_ERR_ARG", ERR_STATE: "PIMC_ERR_STATE", ERR_CUDA: "PIMC_ERR_CUDA",
@@ -27,6 +29,7 @@ _ERRNAMES = {ERR_ARG: "PIMC_ERR_ARG", ERR_STATE: "PIMC_ERR_STATE", ERR_CUDA: "PI
 # Every symbol include/pimc.h declares (checked by the test suite).
 EXPORTS = [
     "pimc_create", "pimc_destroy", "pimc_last_error", "pimc_set_stream", "pimc_set_precision",
+    "pimc_set_scheme", "pimc_set_proposal",
     "pimc_set_data", "pimc_load_data", "pimc_set_params", "pimc_set_path", "pimc_set_steps", "pimc_set_schedule",
     "pimc_set_chain", "pimc_sweep", "pimc_hmc", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
@@ -76,6 +79,8 @@ def _declare(L):
         "pimc_destroy": [_vp],
         "pimc_set_stream": [_vp, _vp],
         "pimc_set_precision": [_vp, _int],
+        "pimc_set_scheme": [_vp, _int],
+        "pimc_set_proposal": [_vp, _int],
         "pimc_set_data": [_vp, _vp, _vp],
         "pimc_load_data": [_vp, _vp, _vp],
         "pimc_set_params": [_vp, _vp, _vp, _vp, _vp, _int],
@@ -168,6 +173,10 @@ class Sampler:
     @classmethod
     def from_problem(cls, prob, precision=FP64):
         s = cls(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf, precision)
+        if getattr(prob, "scheme", 0):
+            s.set_scheme(prob.scheme)
+        if getattr(prob, "proposal", 0):
+            s.set_proposal(prob.proposal)
         s.set_data(prob.y, prob.I)
         s.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
         s.set_steps(prob.sig_x, prob.sig_p)
@@ -194,6 +203,12 @@ class Sampler:
 
     def set_precision(self, precision):
         self._ck(self._L.pimc_set_precision(self._h, int(precision)))
+
+    def set_scheme(self, scheme):
+        self._ck(self._L.pimc_set_scheme(self._h, int(scheme)))
+
+    def set_proposal(self, kind):
+        self._ck(self._L.pimc_set_proposal(self._h, int(kind)))
 
     def set_data(self, y, I):
         self._ck(self._L.pimc_set_data(self._h, _p(_f64(y)), _p(_f64(I))))

@@ -15,10 +15,13 @@ pytestmark = pytest.mark.gpu
 MS = [37, 200, 511, 1000, 2500, 64, 1, 300]
 
 
-def _make(prec, grid1=False):
+def _make(prec, grid1=False, paper=False):
     out = []
     for k, M in enumerate(MS):
-        prob = synth.hh_problem(M, data_seed=100 + k, free="all" if k % 2 == 0 else ("gNa", "gK", "gL"))
+        if paper:
+            prob = synth.paper_problem(min(M, 600), data_seed=100 + k)
+        else:
+            prob = synth.hh_problem(M, data_seed=100 + k, free="all" if k % 2 == 0 else ("gNa", "gK", "gL"))
         s = pimc.Sampler.from_problem(prob, precision=prec)
         s.set_chain(k)
         s.set_schedule(n_init=12, n_skip=3, beta0=0.2, n_cool=8, f_acc=0.4, alpha=0.3)
@@ -28,12 +31,12 @@ def _make(prec, grid1=False):
     return out
 
 
-@pytest.mark.parametrize("prec", [pimc.FP64, pimc.FP32_MIXED])
-def test_batched_chains_equal_single_chain_runs_bitwise(prec):
-    alone = _make(prec, grid1=True)
+@pytest.mark.parametrize("prec,paper", [(pimc.FP64, False), (pimc.FP32_MIXED, False), (pimc.FP64, True)])
+def test_batched_chains_equal_single_chain_runs_bitwise(prec, paper):
+    alone = _make(prec, grid1=True, paper=paper)
     for s in alone:
         s.sweep(25, 77)
-    grouped = _make(prec)
+    grouped = _make(prec, paper=paper)
     b = pimc.Batch(grouped)
     b.set_tuning(256, 0)
     b.sweep(10, 77)

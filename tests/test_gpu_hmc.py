@@ -19,16 +19,18 @@ pytestmark = pytest.mark.gpu
 
 def _oracle(prob):
     ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_scheme(prob.scheme)
     ch.set_data(prob.y, prob.I)
     ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
     return ch
 
 
-@pytest.mark.parametrize("model", ["lg", "hh"])
+@pytest.mark.parametrize("model", ["lg", "hh", "lg_trap"])
 def test_hmc_replay_against_oracle(model):
-    if model == "lg":
+    if model.startswith("lg"):
         prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
-        L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
+        prob.scheme = 1 if model == "lg_trap" else 0
+        L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True, scheme=prob.scheme)
         mu, cov = lgc.posterior(L, r, w)
         inv_mass = np.diag(cov).copy()
         eps, n_leap = 0.2, 12

@@ -19,6 +19,8 @@ pytestmark = pytest.mark.gpu
 
 def oracle_chain(prob):
     ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+    ch.set_scheme(prob.scheme)
+    ch.set_proposal(prob.proposal)
     ch.set_data(prob.y, prob.I)
     ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
     ch.set_steps(prob.sig_x, prob.sig_p)
@@ -37,13 +39,27 @@ def hh(M, seed=0, free=("gNa", "gK", "gL")):
     return synth.hh_problem(M, data_seed=seed, free=free)
 
 
+def trap(prob, proposal=0):
+    prob.scheme = 1
+    prob.proposal = proposal
+    return prob
+
+
 @pytest.mark.parametrize("M", [1, 2, 17, 1000, 4097])
-@pytest.mark.parametrize("model", ["hh", "lg", "toy"])
+@pytest.mark.parametrize("model", ["hh", "lg", "toy", "paper_trap", "hh_trap", "lg_trap"])
 def test_site_delta_parity(M, model):
     if model == "hh":
         prob = hh(M, seed=M)
     elif model == "lg":
         prob = synth.lingauss_problem(M, data_seed=M)
+    elif model == "paper_trap":
+        if M > 1000:
+            pytest.skip("paper-variant generator is slow at this size")
+        prob = synth.paper_problem(M, data_seed=M)
+    elif model == "hh_trap":
+        prob = trap(hh(M, seed=M))
+    elif model == "lg_trap":
+        prob = trap(synth.lingauss_problem(M, data_seed=M))
     else:
         prob = synth.toy_problem(M, data_seed=M, p_free=True)
     X = synth.random_path_near(prob, base_path(prob), 0.5 * prob.sig_x, seed=M)
@@ -59,9 +75,16 @@ def test_site_delta_parity(M, model):
         assert np.all(err <= 1e-12 * scale + 1e-300), (np.argmax(err / (scale + 1e-300)), err.max())
 
 
-@pytest.mark.parametrize("M", [1, 17, 1000, 4097])
-def test_param_delta_action_and_grad_parity(M):
-    prob = hh(M, seed=3, free="all")
+@pytest.mark.parametrize("M,variant", [(1, "hh"), (17, "hh"), (1000, "hh"), (4097, "hh"), (17, "hh_trap"),
+                                       (1000, "hh_trap"), (2, "paper_trap"), (300, "paper_trap"),
+                                       (300, "paper_rk4")])
+def test_param_delta_action_and_grad_parity(M, variant):
+    if variant == "hh":
+        prob = hh(M, seed=3, free="all")
+    elif variant == "hh_trap":
+        prob = trap(hh(M, seed=3, free="all"))
+    else:
+        prob = synth.paper_problem(M, data_seed=3, scheme=1 if variant == "paper_trap" else 0)
     X = synth.random_path_near(prob, base_path(prob), 0.3 * prob.sig_x, seed=7)
     g = pimc.Sampler.from_problem(prob)
     g.set_path(X)
@@ -135,11 +158,23 @@ def test_replay_ragged_tiles(grid):
     assert flips == 0
 
 
-@pytest.mark.parametrize("model", ["lg", "toy"])
+@pytest.mark.parametrize("model", ["lg", "toy", "lg_trap", "toy_trap_uniform"])
 def test_replay_test_models(model):
-    prob = synth.lingauss_problem(50, 1) if model == "lg" else synth.toy_problem(50, 2, p_free=True)
+    if model.startswith("lg"):
+        prob = synth.lingauss_problem(50, 1)
+    else:
+        prob = synth.toy_problem(50, 2, p_free=True)
+    if "trap" in model:
+        trap(prob, proposal=1 if "uniform" in model else 0)
     flips, _ = _replay(prob, 200, seed=4)
     assert flips == 0
+
+
+def test_replay_paper_setting():
+    """The paper's variant: tanh kinetics, trapezoid rule, uniform proposals, 7 free parameters."""
+    prob = synth.paper_problem(400, data_seed=8, free="all")
+    flips, _ = _replay(prob, 150, seed=6)
+    assert flips <= 1
 
 
 def test_sweep_counter_and_annealing_match_oracle():

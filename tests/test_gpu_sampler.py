@@ -19,16 +19,19 @@ from tests import _linear_gaussian as lgc
 pytestmark = pytest.mark.gpu
 
 
-def test_T_LG_gpu_chains_match_closed_form():
+@pytest.mark.parametrize("scheme,proposal", [(0, 0), (1, 1)])
+def test_T_LG_gpu_chains_match_closed_form(scheme, proposal):
     prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
-    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
+    prob.scheme, prob.proposal = scheme, proposal
+    L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True, scheme=scheme)
     mu, cov = lgc.posterior(L, r, w)
     csd = 1.0 / np.sqrt(np.diag(np.linalg.inv(cov)))
     nx = 2 * (prob.M + 1)
     means, vars_ = [], []
     for k in range(16):
         g = pimc.Sampler.from_problem(prob)
-        g.set_steps(csd[:nx].reshape(2, prob.M + 1), np.array([2.0 * csd[-1]]))
+        kk = 1.0 if proposal == 0 else 1.7
+        g.set_steps(kk * csd[:nx].reshape(2, prob.M + 1), np.array([2.0 * kk * csd[-1]]))
         g.set_chain(k)
         g.set_schedule(n_init=3000, n_skip=1)
         g.sweep(3000 + 25000, seed=2024)
