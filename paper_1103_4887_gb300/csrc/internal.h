@@ -45,7 +45,9 @@ struct Ctx {
     uint32_t* acc_win;            // [ldx] accepted moves per site in the adaptation window
     DevState* st;
     double* partials;             // [2][kMaxGrid] per-CTA parameter-move sums
-    unsigned* bar;                // [0] arrivals, [1] generation of the grid barrier
+    unsigned* bar;                // [0] the grid barrier's word
+    unsigned long long* flags;    // [2][kMaxGrid] neighbour epoch flags of the sweep
+    uint64_t ep0;                 // epoch of the sweep before this launch's first (flags only grow)
     unsigned* ticket;             // last-block counter of single-pass reductions
     double* red;                  // [kMaxGrid * 8] per-CTA partials of single-pass reductions
     double *S1, *S2, *shift;      // [D*(M+1) + NP] running shifted sums (FP64)
@@ -87,8 +89,13 @@ template <> constexpr int prec_of<float>() { return 1; }
 void set_thread_error(const char* msg);
 
 // Kernel launchers (model: pimc_model, prec: pimc_precision).
-cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s);
-int sweep_max_grid(int model, int prec, int device);  // co-resident CTAs on the device
+// resident != 0: the resident form where it fits (resident_fits)
+cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s);
+// co-resident CTAs on the device of the general (resident = 0) or resident
+// (resident = 1, FP32-mixed only; 0 otherwise) sweep kernel
+int sweep_max_grid(int model, int prec, int device, int resident);
+// whether a launch of `grid` CTAs with tiles of `tile` sites takes the resident form
+bool resident_fits(int prec, int64_t tile, int grid);
 // Many whole chains in one launch (nt threads per CTA: 128 or 256): CTA b runs
 // chains[order[first[b] .. first[b+1])] one after another.
 cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first, const int* order,

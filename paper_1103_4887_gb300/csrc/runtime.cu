@@ -35,6 +35,9 @@ struct pimc_handle_s {
     DevState* st = nullptr;
     double* partials = nullptr;
     unsigned* bar = nullptr;
+    unsigned long long* flags = nullptr;  // neighbour epoch flags [2][kMaxGrid] of the sweep kernel
+    uint64_t epoch = 0;                   // sweeps launched so far: the flags' epoch base
+    bool resident = false;                // the sweep takes the resident form (one site a thread)
     unsigned* ticket = nullptr;
     double* red = nullptr;
     double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
@@ -104,7 +107,7 @@ Ctx make_ctx(pimc_t h)
     c.dt = h->dt; c.Rm = h->Rm;
     for (int a = 0; a < 4; ++a) c.Rf[a] = h->Rf[a];
     c.X = h->X; c.F[0] = h->F[0]; c.F[1] = h->F[1]; c.y = h->y; c.I = h->I; c.sig = h->sig;
-    c.acc_win = h->acc_win; c.st = h->st; c.partials = h->partials; c.bar = h->bar;
+    c.acc_win = h->acc_win; c.st = h->st; c.partials = h->partials; c.bar = h->bar; c.flags = h->flags;
     c.ticket = h->ticket; c.red = h->red;
     c.S1 = h->S1; c.S2 = h->S2; c.shift = h->shift;
     c.R1 = h->R1; c.R2 = h->R2;
@@ -192,7 +195,7 @@ int refresh(pimc_t h)
 void choose_grid(pimc_t h)
 {
     const int64_t sites = h->M + 1;
-    int maxco = sweep_max_grid(h->model, h->prec, h->device);
+    int maxco = sweep_max_grid(h->model, h->prec, h->device, 0);
     if (maxco < 1) maxco = 1;
     if (maxco > kMaxGrid) maxco = kMaxGrid;
     int64_t g;
@@ -206,7 +209,12 @@ void choose_grid(pimc_t h)
     if (g > maxco) g = maxco;
     if (g < 1) g = 1;
     h->tile = (sites + g - 1) / g;
+    // tiles of even length when tiled: every CTA's first site is even, so a
+    // tile's halo sites change in fixed phases of the sweep
+    if (g > 1) h->tile += h->tile & 1;
     h->grid = (int)((sites + h->tile - 1) / h->tile);
+    h->resident = resident_fits(h->prec, h->tile, h->grid) &&
+                  h->grid <= sweep_max_grid(h->model, h->prec, h->device, 1);
 }
 
 int check_finite(const double* v, int64_t n)
@@ -218,7 +226,7 @@ int check_finite(const double* v, int64_t n)
 
 void free_all(pimc_t h)
 {
-    void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar,
+    void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar, h->flags,
                     h->ticket, h->red, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
                     h->dense, h->small, h->y64, h->I64, h->trace, h->R1, h->R2, h->hmc.hs, h->hmc.Q, h->hmc.P,
                     h->hmc.g, h->hmc.invm};
@@ -294,6 +302,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         {(void**)&h->st, sizeof(DevState)},
         {(void**)&h->partials, sizeof(double) * 2 * kMaxGrid},
         {(void**)&h->bar, sizeof(unsigned) * 4},
+        {(void**)&h->flags, sizeof(unsigned long long) * 2 * kMaxGrid},
         {(void**)&h->ticket, sizeof(unsigned) * 4},
         {(void**)&h->red, sizeof(double) * 8 * kMaxGrid},
         {(void**)&h->S1, sizeof(double) * nc},
@@ -318,6 +327,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         }
     }
     cudaMemset(h->bar, 0, sizeof(unsigned) * 4);
+    cudaMemset(h->flags, 0, sizeof(unsigned long long) * 2 * kMaxGrid);
     cudaMemset(h->ticket, 0, sizeof(unsigned) * 4);
     cudaMemset(h->X, 0, sizeof(double) * D * h->ldx);
     cudaMemset(h->F[0], 0, sizeof(double) * D * h->ldf);
@@ -530,7 +540,9 @@ int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed)
     const int64_t chunk = 4096;  // bound the duration of one launch
     for (int64_t done = 0; done < n_sweeps; done += chunk) {
         const int64_t k = std::min<int64_t>(chunk, n_sweeps - done);
-        CK(h, launch_sweep(h->model, h->prec, c, k, h->grid, h->stream));
+        c.ep0 = h->epoch;
+        CK(h, launch_sweep(h->model, h->prec, c, k, h->grid, h->resident ? 1 : 0, h->stream));
+        h->epoch += (uint64_t)k;
     }
     return PIMC_OK;
 }

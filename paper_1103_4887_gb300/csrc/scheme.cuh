@@ -26,12 +26,23 @@ template <class R> struct Coef {
 // vector field F(x_n) (trapezoid rule, n <= M; the drive at t_M is I_{M-1}).
 __device__ __forceinline__ int64_t cache_len(const Ctx& c) { return c.scheme == kSchemeRK4 ? c.M : c.M + 1; }
 
+__device__ __forceinline__ int64_t drive_index(const Ctx& c, int64_t n)
+{
+    return (c.scheme == kSchemeRK4 || n < c.M) ? n : c.M - 1;
+}
+
+// Cached value from a drive value already loaded.
+template <class Model, class R>
+__device__ __forceinline__ void cache_value_at(const Ctx& c, const Coef<R>& k, const R* x, const R* q, R drive, R* g)
+{
+    if (c.scheme == kSchemeRK4) rk4_map<Model, R>(x, q, drive, k.dt, g);
+    else Model::rhs(x, q, drive, g);
+}
+
 template <class Model, class R>
 __device__ __forceinline__ void cache_value(const Ctx& c, const Coef<R>& k, const R* x, const R* q, int64_t n, R* g)
 {
-    const R* I = (const R*)c.I;
-    if (c.scheme == kSchemeRK4) rk4_map<Model, R>(x, q, I[n], k.dt, g);
-    else Model::rhs(x, q, I[n < c.M ? n : c.M - 1], g);
+    cache_value_at<Model, R>(c, k, x, q, ((const R*)c.I)[drive_index(c, n)], g);
 }
 
 // Model-error residual eps_{n+1} from x_n, x_{n+1} and their cached values:

@@ -1,12 +1,25 @@
 // The hot path: one persistent cooperative kernel runs whole checkerboard
-// sweeps (Fig. 1, Sec. 4.1).  Each CTA owns a contiguous tile of time steps.
-// Per sweep: even sites, grid barrier, odd sites, grid barrier, then each free
-// parameter in order -- every CTA computes the RK4 map at the proposed p for
-// its sites into the inactive half of the double-buffered f cache (Sec. 4.3)
-// and a partial change of action; after one grid barrier every CTA sums all
-// partials in the same fixed order (FP64) and takes the same accept decision,
-// so no second launch or broadcast is needed.  Statistics, step adaptation and
-// annealing follow in the same launch.  Barrier waits are bounded in time.
+// sweeps (Fig. 1, Sec. 4.1).  Each CTA owns a contiguous tile of time steps;
+// per sweep the even sites move, then the odd sites, then each free parameter
+// in order, then statistics, step adaptation and annealing (Sec. 4.1-4.2).
+//
+// A parameter move (Sec. 4.3) needs the whole path: every CTA evaluates the
+// map at the proposed p for its sites into the inactive half of the
+// double-buffered cache and a partial change of action; after one grid
+// barrier every CTA sums all partials in the same fixed order (FP64) and takes
+// the same accept decision, so no second launch or broadcast is needed.
+//
+// Two forms of the site phases:
+//  * resident (tiles of at most NT - 32 sites): thread 32 + i owns site
+//    n0 + i for the whole launch and keeps its operands in registers; the
+//    tile's neighbours are exchanged through shared memory and the two halo
+//    sites through global memory, ordered by epoch flags between neighbouring
+//    CTAs instead of grid barriers.  Warp 0 draws, reduces, synchronises and
+//    decides; while it waits for the other CTAs, the site threads evaluate the
+//    next parameter move's map for both outcomes of the pending decision.
+//  * general (any tile): threads stride over the tile, operands are read from
+//    global memory (L2), a grid barrier ends each site phase.
+// All waits are bounded in time.
 #include <cuda/atomic>
 
 #include "device.cuh"
@@ -29,8 +42,12 @@ template <class R, int NT> struct SweepShared {
     R q_new[kMaxP][kMaxP];            // proposed vector for each parameter move, in R
     R tpart[NT];                    // per-thread partial sums of a parameter move
     R halo[kMaxD];                  // trapezoid: F(x_{n1}, p') of the next tile's first site
+    R xs[kMaxD][NT];                // resident form: x of site n0 + i at [a][i]
+    R gs[kMaxD][NT];                // resident form: cached value of site n0 + i at [a][i]
     double cta_total;               // CTA sum of a parameter move (CTA-local chains)
+    unsigned long long ep0;         // resident form: epoch base of the neighbour flags
     int abort;
+    int last_acc;                   // outcome of the latest parameter decision
     unsigned long long site_acc[2], site_prop[2], nonfinite;
     long long tr_n;
 };
@@ -42,43 +59,79 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+__device__ __forceinline__ void wait_expired(const Ctx& c)
+{
+    atomicOr(&c.st->status, kStatusTimeout);
+    atomicExch(&c.st->abort, 1);
+}
+
 // Grid-wide barrier on one 32-bit word: every CTA adds 1, except CTA 0 which
 // adds 2^31 - (G - 1), so the word's top bit flips exactly when all G CTAs
 // have arrived and its low bits return to their old value.  Each CTA waits for
 // the flip relative to the value its own add returned (a fence before the add
 // publishes the CTA's writes; a fence after the wait orders its later reads).
 // The wait is bounded by c.wait_ns: on expiry the CTA flags kStatusTimeout and
-// the abort word, and every CTA leaves the launch at its next barrier.
-// Returns false when leaving.
+// the abort word, and every CTA leaves the launch at its next wait.
+__device__ __forceinline__ unsigned grid_arrive(const Ctx& c)
+{
+    const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+    __threadfence();
+    if ((int)blockIdx.x != c.skip_cta) return atomicAdd(&c.bar[0], add);
+    return *(volatile unsigned*)&c.bar[0];
+}
+
+__device__ __forceinline__ bool grid_wait(const Ctx& c, unsigned old)
+{
+    bool ok = true;
+    unsigned spins = 0;
+    const unsigned long long t0 = global_ns();
+    while (((old ^ *(volatile unsigned*)&c.bar[0]) & 0x80000000u) == 0u) {
+        if ((++spins & 63u) == 0u) {
+            if (*(volatile int*)&c.st->abort) { ok = false; break; }
+            if ((long long)(global_ns() - t0) > c.wait_ns) { wait_expired(c); ok = false; break; }
+            if (spins > 4096u) __nanosleep(64);
+        }
+    }
+    __threadfence();
+    return ok;
+}
+
+// Whole-CTA form.  Returns false when leaving.
 __device__ bool grid_barrier(const Ctx& c, int* s_abort)
 {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
-        __threadfence();
-        unsigned old = 0u;
-        if ((int)blockIdx.x != c.skip_cta) old = atomicAdd(&c.bar[0], add);
-        else old = *(volatile unsigned*)&c.bar[0];
-        unsigned spins = 0;
-        const unsigned long long t0 = global_ns();
-        while (((old ^ *(volatile unsigned*)&c.bar[0]) & 0x80000000u) == 0u) {
-            if ((++spins & 63u) == 0u) {
-                if (*(volatile int*)&c.st->abort) { ok = 0; break; }
-                if ((long long)(global_ns() - t0) > c.wait_ns) {
-                    atomicOr(&c.st->status, kStatusTimeout);
-                    atomicExch(&c.st->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 4096u) __nanosleep(64);
-            }
-        }
-        __threadfence();
-        *s_abort = !ok;
-    }
+    if (threadIdx.x == 0) *s_abort = !grid_wait(c, grid_arrive(c));
     __syncthreads();
     return !*s_abort;
+}
+
+// Epoch flags between neighbouring CTAs (resident form).  After its sites of
+// parity ph have moved in the sweep with epoch e, a CTA stores e into
+// flags[ph][b] (a fence first publishes its writes); a neighbour waits,
+// bounded, until the flag reaches e.  Epochs only grow over a handle's
+// launches (the host passes the base in c.ep0).
+__device__ __forceinline__ void flag_post(const Ctx& c, int ph, unsigned long long e)
+{
+    if ((int)blockIdx.x == c.skip_cta) return;
+    __threadfence();
+    *(volatile unsigned long long*)&c.flags[ph * kMaxGrid + blockIdx.x] = e;
+}
+
+__device__ __forceinline__ bool flag_wait(const Ctx& c, int ph, int b, unsigned long long e)
+{
+    bool ok = true;
+    unsigned spins = 0;
+    const unsigned long long t0 = global_ns();
+    const volatile unsigned long long* f = &c.flags[ph * kMaxGrid + b];
+    while (*f < e) {
+        if ((++spins & 63u) == 0u) {
+            if (*(volatile int*)&c.st->abort) { ok = false; break; }
+            if ((long long)(global_ns() - t0) > c.wait_ns) { wait_expired(c); ok = false; break; }
+            if (spins > 4096u) __nanosleep(64);
+        }
+    }
+    __threadfence();
+    return ok;
 }
 
 // Neighbourhood of site n loaded before its map is evaluated.
@@ -168,8 +221,31 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
     u = Num<R>::uni(w.x, w.y);
 }
 
-// One site move: proposal, its cached value, Delta A_n, Metropolis (as
-// dA < -log u, Eq. (Paccept)), store on accept.
+// One site move from operands in registers: proposal x' = x + sigma z, its
+// cached value, Delta A_n, and the Metropolis decision written as
+// dA < -log u (Eq. (Paccept); NaN compares false).
+template <class Model, class R>
+__device__ __forceinline__ bool site_core(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
+                                          R beta, const R* x, const R* sg, R drive, const Nbhd<R, Model::D>& nb,
+                                          R* xp, R* gp, unsigned long long& nonfinite)
+{
+    constexpr int D = Model::D;
+    R z[D], u;
+    site_draws<Model, R>(c, s, n, z, u);
+    const R E = neglog<R>(u);
+#pragma unroll
+    for (int a = 0; a < D; ++a) xp[a] = x[a] + sg[a] * z[a];
+    if (n < cache_len(c)) cache_value_at<Model, R>(c, k, xp, pr, drive, gp);
+    else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gp[a] = R(0);
+    }
+    const R dA = site_delta<Model, R>(c, k, n, x, xp, gp, beta, nb);
+    if (!isfinite(dA)) ++nonfinite;
+    return dA < E;
+}
+
+// General form of a site move: operands from global memory, store on accept.
 template <class Model, class R>
 __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
                                           R beta, R* Fc, unsigned long long& nonfinite)
@@ -177,24 +253,17 @@ __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_
     constexpr int D = Model::D;
     R* X = (R*)c.X;
     const R* sig = (const R*)c.sig;
-    R x[D], xp[D], gp[D], z[D], u;
+    R x[D], sg[D], xp[D], gp[D];
     Nbhd<R, D> nb;
 #pragma unroll
-    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
-    load_nbhd<Model, R>(c, n, Fc, nb);
-    site_draws<Model, R>(c, s, n, z, u);
-    const R E = neglog<R>(u);
-#pragma unroll
-    for (int a = 0; a < D; ++a) xp[a] = x[a] + sig[a * c.ldx + n] * z[a];
-    const bool cached = n < cache_len(c);
-    if (cached) cache_value<Model, R>(c, k, xp, pr, n, gp);
-    else {
-#pragma unroll
-        for (int a = 0; a < D; ++a) gp[a] = R(0);
+    for (int a = 0; a < D; ++a) {
+        x[a] = X[a * c.ldx + n];
+        sg[a] = sig[a * c.ldx + n];
     }
-    const R dA = site_delta<Model, R>(c, k, n, x, xp, gp, beta, nb);
-    if (!isfinite(dA)) ++nonfinite;
-    const bool acc = dA < E;
+    load_nbhd<Model, R>(c, n, Fc, nb);
+    const bool cached = n < cache_len(c);
+    const R drive = cached ? ((const R*)c.I)[drive_index(c, n)] : R(0);
+    const bool acc = site_core<Model, R>(c, k, n, s, pr, beta, x, sg, drive, nb, xp, gp, nonfinite);
     if (acc) {
 #pragma unroll
         for (int a = 0; a < D; ++a) X[a * c.ldx + n] = xp[a];
@@ -202,7 +271,7 @@ __device__ __forceinline__ bool site_move(const Ctx& c, const Coef<R>& k, int64_
 #pragma unroll
             for (int a = 0; a < D; ++a) Fc[a * c.ldf + n] = gp[a];
         }
-        c.acc_win[n] += 1u;
+        atomicAdd(&c.acc_win[n], 1u);
     }
     return acc;
 }
@@ -289,94 +358,223 @@ __device__ __forceinline__ double block_sum(double v, double* wsum)
     return t;
 }
 
+// Warp 0: FP64 sum of the NT per-thread partials of a parameter move, from the
+// per-thread values up (pairwise within a lane, then across lanes); valid in
+// lane 0.
+template <class R, int NT>
+__device__ __forceinline__ double cta_partial(const R* tpart, int lane)
+{
+    double t[NT / 32];
+#pragma unroll
+    for (int q = 0; q < NT / 32; ++q) t[q] = (double)tpart[lane + 32 * q];
+#pragma unroll
+    for (int w = NT / 64; w >= 1; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) t[q] += t[q + w];
+    return warp_sum(t[0]);
+}
+
 // Synchronisation policies of a chain's sweep.  GridSync: the chain is tiled
 // over all CTAs of a cooperative launch (grid barriers, every CTA sums all CTA
 // partials in the same order).  BlockSync: one CTA owns the whole chain
 // (CTA barriers, the CTA sum is the total).  With one CTA both give the same
 // bits.
 struct GridSync {
+    static constexpr bool tiled = true;
     __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort) const { return grid_barrier(c, s_abort); }
+    __device__ __forceinline__ bool arrive_wait(const Ctx& c) const { return grid_wait(c, grid_arrive(c)); }
     __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, double v, double*) const
     {
         c.partials[slot * kMaxGrid + blockIdx.x] = v;
     }
+    // Warp-wide: every lane loads its CTAs' partials (independent loads, one
+    // L2 round trip), then a fixed-order sum; valid in every lane.
     __device__ __forceinline__ double gather(const Ctx& c, unsigned slot, int lane, const double*) const
     {
+        const int G = (int)gridDim.x;
+        const double* part = c.partials + slot * kMaxGrid;
         double v = 0.0;
-        for (int i = lane; i < (int)gridDim.x; i += 32) v += __ldcg(&c.partials[slot * kMaxGrid + i]);
-        return warp_sum(v);
+        for (int base = 0; base < G; base += 512) {
+            double t[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int i = base + lane + 32 * j;
+                t[j] = (i < G) ? __ldcg(part + i) : 0.0;
+            }
+#pragma unroll
+            for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                for (int j = 0; j < w; ++j) t[j] += t[j + w];
+            v += t[0];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        return v;
     }
     __device__ __forceinline__ bool lead() const { return blockIdx.x == 0; }
 };
 
 struct BlockSync {
+    static constexpr bool tiled = false;
     __device__ __forceinline__ bool barrier(const Ctx&, int*) const
     {
         __syncthreads();
         return true;
     }
+    __device__ __forceinline__ bool arrive_wait(const Ctx&) const { return true; }
     __device__ __forceinline__ void publish(const Ctx&, unsigned, double v, double* total) const { *total = v; }
-    __device__ __forceinline__ double gather(const Ctx&, unsigned, int lane, const double* total) const
+    __device__ __forceinline__ double gather(const Ctx&, unsigned, int, const double* total) const
     {
-        return warp_sum(lane == 0 ? *total : 0.0);
+        return *(volatile const double*)total;
     }
     __device__ __forceinline__ bool lead() const { return true; }
 };
 
+// ---- pieces shared by both forms --------------------------------------------
+
+template <class Model, class R, int NT>
+__device__ __forceinline__ void load_chain_state(const Ctx& c, SweepShared<R, NT>& sh)
+{
+    const DevState* g = c.st;
+    for (int l = 0; l < kMaxP; ++l) {
+        sh.p[l] = g->p[l]; sh.lo[l] = g->lo[l]; sh.hi[l] = g->hi[l]; sh.sigp[l] = g->sigp[l];
+        sh.accp_win[l] = g->accp_win[l]; sh.par_acc[l] = g->par_acc[l]; sh.par_prop[l] = g->par_prop[l];
+    }
+    sh.beta = g->beta; sh.sweep = g->sweep; sh.J = g->J; sh.fidx = g->fidx;
+    sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0; sh.tr_n = g->tr_n; sh.last_acc = 0;
+    sh.site_acc[0] = sh.site_acc[1] = sh.site_prop[0] = sh.site_prop[1] = sh.nonfinite = 0ull;
+    sh.ep0 = c.ep0;
+    Model::prep(sh.p, sh.q_cur);
+}
+
+// This sweep's proposal for parameter l (one thread per parameter).  p_l
+// changes only in its own move, so p'_l = p_l + sigma_l z_l is fixed at the
+// sweep's start; the proposed vector of move l is completed after the earlier
+// moves from q_new[l] (components l, and 7 with l = 6).
+template <class Model, class R, int NT>
+__device__ __forceinline__ void draw_param_proposal(const Ctx& c, SweepShared<R, NT>& sh, long long s, int l)
+{
+    if (!((sh.free_mask >> l) & 1u)) return;
+    double z0, z1;
+    const uint4 wz = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u);
+    if (c.proposal == kProposalUniform) z0 = 2.0 * u01d(wz.x, wz.y) - 1.0;
+    else Num<double>::box_muller(wz, z0, z1);
+    const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
+    const double pl = sh.p[l] + sh.sigp[l] * z0;
+    sh.pnew[l] = pl;
+    sh.elog[l] = -log(u01d(w.x, w.y));
+    sh.inbox[l] = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
+    double pv[kMaxP];
+    for (int q = 0; q < kMaxP; ++q) pv[q] = sh.p[q];
+    pv[l] = pl;
+    Model::prep(pv, sh.q_new[l]);
+}
+
+// The model-parameter vector of move l applied to q.
+template <class R, int NT>
+__device__ __forceinline__ void apply_move(R* q, const SweepShared<R, NT>& sh, int l)
+{
+    q[l] = sh.q_new[l][l];
+    if (l == 6) q[7] = sh.q_new[6][7];
+}
+
+// Decision of move l on the total change of action v: Eq. (Paccept) as
+// dA < -log u (NaN compares false).  One thread.
+template <class R, int NT>
+__device__ __forceinline__ void decide(SweepShared<R, NT>& sh, int l, double v)
+{
+    const int acc = (v < sh.elog[l]) ? 1 : 0;
+    if (acc) {
+        sh.p[l] = sh.pnew[l];
+        sh.q_cur[l] = sh.q_new[l][l];
+        if (l == 6) sh.q_cur[7] = sh.q_new[l][7];
+        sh.fidx ^= 1u;
+        sh.accp_win[l] += 1u;
+        sh.par_acc[l] += 1ull;
+    }
+    sh.last_acc = acc;
+    sh.nred += 1u;
+}
+
+// Step adaptation of the parameters during burn-in (Sec. 4.2).  One thread.
+template <int NP, class R, int NT>
+__device__ __forceinline__ void adapt_params(const Ctx& c, SweepShared<R, NT>& sh)
+{
+    for (int l = 0; l < NP; ++l) {
+        if ((sh.free_mask >> l) & 1u)
+            sh.sigp[l] *= 1.0 + c.alpha * ((double)sh.accp_win[l] / (double)c.n_skip - c.f_acc);
+        sh.accp_win[l] = 0u;
+    }
+}
+
+// End of a sweep: parameter trace, annealing (Eq. (fbeta)), counters.
+template <int NP, class R, int NT, class Sync>
+__device__ __forceinline__ void end_sweep(const Ctx& c, SweepShared<R, NT>& sh, long long s, bool record,
+                                          const Sync& sync)
+{
+    const int tid = threadIdx.x;
+    if (c.trace && sync.lead() && tid < NP) c.trace[(sh.tr_n % c.trace_cap) * NP + tid] = sh.p[tid];
+    __syncthreads();
+    if (tid == 0) {
+        sh.beta = (s + 1 < c.n_cool) ? sh.beta * c.fbeta : 1.0;
+        sh.sweep = s + 1;
+        if (record) sh.J += 1;
+        if (c.trace) sh.tr_n += 1;
+    }
+    __syncthreads();
+}
+
+// Adds this CTA's counters and (lead CTA) writes the chain state back.
+template <class R, int NT, class Sync>
+__device__ __forceinline__ void store_chain_state(const Ctx& c, SweepShared<R, NT>& sh, const Sync& sync,
+                                                  const unsigned long long* acc, const unsigned long long* prop,
+                                                  unsigned long long nf)
+{
+    __syncthreads();
+    atomicAdd(&sh.site_acc[0], acc[0]);
+    atomicAdd(&sh.site_acc[1], acc[1]);
+    atomicAdd(&sh.site_prop[0], prop[0]);
+    atomicAdd(&sh.site_prop[1], prop[1]);
+    atomicAdd(&sh.nonfinite, nf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevState* g = c.st;
+        atomicAdd(&g->site_acc[0], sh.site_acc[0]);
+        atomicAdd(&g->site_acc[1], sh.site_acc[1]);
+        atomicAdd(&g->site_prop[0], sh.site_prop[0]);
+        atomicAdd(&g->site_prop[1], sh.site_prop[1]);
+        atomicAdd(&g->nonfinite, sh.nonfinite);
+        if (sync.lead()) {
+            for (int l = 0; l < kMaxP; ++l) {
+                g->p[l] = sh.p[l]; g->sigp[l] = sh.sigp[l]; g->accp_win[l] = sh.accp_win[l];
+                g->par_acc[l] = sh.par_acc[l]; g->par_prop[l] = sh.par_prop[l];
+            }
+            g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx; g->tr_n = sh.tr_n;
+        }
+    }
+    __syncthreads();
+}
+
+// ---- general form -----------------------------------------------------------
+
 // n_sweeps checkerboard sweeps of one chain over the sites [n0, n1) this CTA
-// owns: loads the chain's scalar state, runs the sweeps, writes it back (the
-// lead CTA) and adds this CTA's counters.
+// owns, threads striding over the tile.
 template <class Model, class R, int NT, class Sync>
-__device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
-                            const Sync& sync)
+__device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
+                                    const Sync& sync)
 {
     constexpr int D = Model::D, NP = Model::NP;
     const int tid = threadIdx.x;
     const Coef<R> kc(c);
-    if (tid == 0) {
-        const DevState* g = c.st;
-        for (int l = 0; l < kMaxP; ++l) {
-            sh.p[l] = g->p[l]; sh.lo[l] = g->lo[l]; sh.hi[l] = g->hi[l]; sh.sigp[l] = g->sigp[l];
-            sh.accp_win[l] = g->accp_win[l]; sh.par_acc[l] = g->par_acc[l]; sh.par_prop[l] = g->par_prop[l];
-        }
-        sh.beta = g->beta; sh.sweep = g->sweep; sh.J = g->J; sh.fidx = g->fidx;
-        sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0; sh.tr_n = g->tr_n;
-        sh.site_acc[0] = sh.site_acc[1] = sh.site_prop[0] = sh.site_prop[1] = sh.nonfinite = 0ull;
-        Model::prep(sh.p, sh.q_cur);
-    }
-    __syncthreads();
-
     const int64_t M = c.M;
     unsigned long long my_acc[2] = {0ull, 0ull}, my_prop[2] = {0ull, 0ull}, my_nf = 0ull;
-    R* X = (R*)c.X;
     R* sig = (R*)c.sig;
 
     for (int64_t k = 0; k < n_sweeps; ++k) {
         const long long s = sh.sweep;
-        // This sweep's parameter proposals, one lane per parameter of the last
-        // warp (idle in the site phases at small M).  p_l changes only in its
-        // own move, so p'_l = p_l + sigma_l z_l is fixed at the sweep's start;
-        // the proposed vector for move l is completed after the earlier moves.
-        if (tid >= NT - 32 && tid - (NT - 32) < NP) {
-            const int l = tid - (NT - 32);
-            if ((sh.free_mask >> l) & 1u) {
-                double z0, z1;
-                const uint4 wz = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u);
-                if (c.proposal == kProposalUniform) z0 = 2.0 * u01d(wz.x, wz.y) - 1.0;
-                else Num<double>::box_muller(wz, z0, z1);
-                const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
-                const double pl = sh.p[l] + sh.sigp[l] * z0;
-                sh.pnew[l] = pl;
-                sh.elog[l] = -log(u01d(w.x, w.y));
-                sh.inbox[l] = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
-                double pv[kMaxP];
-                for (int q = 0; q < kMaxP; ++q) pv[q] = sh.p[q];
-                pv[l] = pl;
-                Model::prep(pv, sh.q_new[l]);
-            }
-        }
-        // (no barrier here: the draws overlap the even site phase and are
-        // published by the barrier that ends it)
+        // proposals by the last warp (idle in the site phases at small M); no
+        // barrier here: the barrier that ends the even phase publishes them
+        if (tid >= NT - 32 && tid - (NT - 32) < NP) draw_param_proposal<Model, R, NT>(c, sh, s, tid - (NT - 32));
         const R beta = R(sh.beta);
         R pr[kMaxP];
 #pragma unroll
@@ -400,7 +598,8 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
             if (!sh.inbox[l]) continue;  // out of the prior box: rejected without compute
             R pq[kMaxP];
 #pragma unroll
-            for (int q = 0; q < kMaxP; ++q) pq[q] = (q == l || (q == 7 && l == 6)) ? sh.q_new[l][q] : pr[q];
+            for (int q = 0; q < kMaxP; ++q) pq[q] = pr[q];
+            apply_move<R, NT>(pq, sh, l);
             const R* Fc = (const R*)c.F[sh.fidx];
             R* Fn = (R*)c.F[sh.fidx ^ 1u];
             R part = R(0);
@@ -425,36 +624,17 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
                     part += trap_term<Model, R>(c, kc, n, beta, Fc, Fn, gn1p);
                 }
             }
-            // CTA sum in FP64 from the per-thread partials up, by one warp (pairwise within a lane)
             sh.tpart[tid] = part;
             __syncthreads();
             const unsigned slot = sh.nred & 1u;
             if (tid < 32) {
-                double t[NT / 32];
-#pragma unroll
-                for (int q = 0; q < NT / 32; ++q) t[q] = (double)sh.tpart[tid + 32 * q];
-#pragma unroll
-                for (int w = NT / 64; w >= 1; w >>= 1)
-#pragma unroll
-                    for (int q = 0; q < w; ++q) t[q] += t[q + w];
-                const double v = warp_sum(t[0]);
+                const double v = cta_partial<R, NT>(sh.tpart, tid);
                 if (tid == 0) sync.publish(c, slot, v, &sh.cta_total);
             }
             if (!sync.barrier(c, &sh.abort)) goto done;
             if (tid < 32) {
                 const double v = sync.gather(c, slot, tid, &sh.cta_total);
-                if (tid == 0) {
-                    // Eq. (Paccept) as dA < -log u (NaN compares false)
-                    if (v < sh.elog[l]) {
-                        sh.p[l] = sh.pnew[l];
-                        sh.q_cur[l] = sh.q_new[l][l];
-                        if (l == 6) sh.q_cur[7] = sh.q_new[l][7];
-                        sh.fidx ^= 1u;
-                        sh.accp_win[l] += 1u;
-                        sh.par_acc[l] += 1ull;
-                    }
-                    sh.nred += 1u;
-                }
+                if (tid == 0) decide<R, NT>(sh, l, v);
             }
             __syncthreads();
 #pragma unroll
@@ -462,67 +642,354 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
         }
         __syncthreads();
 
-        // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
-        const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
-        if (record)
-            record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
+        {
+            // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
+            // (the residual of the tile's last site reads the next tile's first
+            // site: a barrier keeps it unchanged until every CTA has recorded)
+            const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
+            if (record) {
+                record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
+                if (!sync.barrier(c, &sh.abort)) goto done;
+            }
 
-        // ---- step-size adaptation during burn-in (Sec. 4.2) ----
-        if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
-            for (int64_t n = n0 + tid; n < n1; n += NT) {
-                const double fac = 1.0 + c.alpha * ((double)c.acc_win[n] / (double)c.n_skip - c.f_acc);
+            // ---- step-size adaptation during burn-in (Sec. 4.2) ----
+            if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
+                for (int64_t n = n0 + tid; n < n1; n += NT) {
+                    const double fac = 1.0 + c.alpha * ((double)c.acc_win[n] / (double)c.n_skip - c.f_acc);
 #pragma unroll
-                for (int a = 0; a < D; ++a) sig[a * c.ldx + n] = R((double)sig[a * c.ldx + n] * fac);
-                c.acc_win[n] = 0u;
-            }
-            if (tid == 0) {
-                for (int l = 0; l < NP; ++l) {
-                    if ((sh.free_mask >> l) & 1u)
-                        sh.sigp[l] *= 1.0 + c.alpha * ((double)sh.accp_win[l] / (double)c.n_skip - c.f_acc);
-                    sh.accp_win[l] = 0u;
+                    for (int a = 0; a < D; ++a) sig[a * c.ldx + n] = R((double)sig[a * c.ldx + n] * fac);
+                    c.acc_win[n] = 0u;
                 }
+                if (tid == 0) adapt_params<NP>(c, sh);
             }
+            end_sweep<NP>(c, sh, s, record, sync);
         }
-
-        // ---- parameter trace (for effective-sample-size diagnostics) ----
-        if (c.trace && sync.lead() && tid < NP)
-            c.trace[(sh.tr_n % c.trace_cap) * NP + tid] = sh.p[tid];
-
-        // ---- annealing, Eq. (fbeta): beta_{s+1} = beta_s f_beta until N_cool ----
-        __syncthreads();
-        if (tid == 0) {
-            sh.beta = (s + 1 < c.n_cool) ? sh.beta * c.fbeta : 1.0;
-            sh.sweep = s + 1;
-            if (record) sh.J += 1;
-            if (c.trace) sh.tr_n += 1;
-        }
-        __syncthreads();
     }
 
 done:
-    __syncthreads();
-    atomicAdd(&sh.site_acc[0], my_acc[0]);
-    atomicAdd(&sh.site_acc[1], my_acc[1]);
-    atomicAdd(&sh.site_prop[0], my_prop[0]);
-    atomicAdd(&sh.site_prop[1], my_prop[1]);
-    atomicAdd(&sh.nonfinite, my_nf);
-    __syncthreads();
-    if (tid == 0) {
-        DevState* g = c.st;
-        atomicAdd(&g->site_acc[0], sh.site_acc[0]);
-        atomicAdd(&g->site_acc[1], sh.site_acc[1]);
-        atomicAdd(&g->site_prop[0], sh.site_prop[0]);
-        atomicAdd(&g->site_prop[1], sh.site_prop[1]);
-        atomicAdd(&g->nonfinite, sh.nonfinite);
-        if (sync.lead()) {
-            for (int l = 0; l < kMaxP; ++l) {
-                g->p[l] = sh.p[l]; g->sigp[l] = sh.sigp[l]; g->accp_win[l] = sh.accp_win[l];
-                g->par_acc[l] = sh.par_acc[l]; g->par_prop[l] = sh.par_prop[l];
-            }
-            g->beta = sh.beta; g->sweep = sh.sweep; g->J = sh.J; g->fidx = sh.fidx; g->tr_n = sh.tr_n;
+    store_chain_state(c, sh, sync, my_acc, my_prop, my_nf);
+}
+
+// ---- resident form ------------------------------------------------------------
+
+// Values of site n for one parameter vector q: RK4, f(x_n) (n < M);
+// trapezoid, F(x_n) and the neighbour's F(x_{n+1}) (n < M).
+template <class Model, class R>
+__device__ __forceinline__ void move_values(const Ctx& c, const Coef<R>& k, bool trap, bool has_next, const R* x,
+                                            const R* xn, R drive, R drive1, const R* q, R* f, R* fn)
+{
+    if (!trap) {
+        if (has_next) rk4_map<Model, R>(x, q, drive, k.dt, f);
+    } else {
+        Model::rhs(x, q, drive, f);
+        if (has_next) Model::rhs(xn, q, drive1, fn);
+    }
+}
+
+// Change of the model-error term eps_{n+1} when the cached values of n (and
+// n+1 under the trapezoid rule) become f (fn).
+template <class R, int D>
+__device__ __forceinline__ R move_term(const Ctx& c, const Coef<R>& k, bool trap, const R* x, const R* xn,
+                                       const R* g, const R* gn, const R* f, const R* fn, R beta)
+{
+    R t = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (!trap) {
+            t += beta * sqdiff<R>(k.Rf[a], xn[a] - f[a], xn[a] - g[a]);
+        } else {
+            const R e = eps_of<R>(c, k, x[a], xn[a], g[a], gn[a]);
+            const R ep = eps_of<R>(c, k, x[a], xn[a], f[a], fn[a]);
+            t += beta * sqdiff<R>(k.Rf[a], ep, e);
         }
     }
+    return t;
+}
+
+template <class Model, class R, int NT, class Sync>
+__device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
+                                     const Sync& sync)
+{
+    constexpr int D = Model::D, NP = Model::NP;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const Coef<R> kc(c);
+    const int64_t M = c.M, T = n1 - n0;
+    const int i = tid - 32;
+    const int64_t n = n0 + i;
+    const bool own = tid >= 32 && i < T;
+    const bool trap = c.scheme != kSchemeRK4;
+    const int64_t clen = cache_len(c);
+    const bool cached = own && n < clen;
+    const bool has_next = own && n < M;          // site n carries eps_{n+1}
+    const bool left_halo = own && i == 0 && n0 >= 1;
+    const bool right_halo = own && i == T - 1 && n1 <= M;
+    const int b = (int)blockIdx.x;
+    // partial of site n0 + i at tpart[i], zeros above the tile (warp 0 fills
+    // the top 32): the CTA sum then adds in the general form's order
+    const int tslot = (tid >= 32) ? i : NT - 32 + tid;
+    R* X = (R*)c.X;
+    R* sig = (R*)c.sig;
+
+    // registers of the owned site
+    R xr[D], sgr[D], gr[D], xh[D], gh[D];
+    R yv = R(0), drive = R(0), drive1 = R(0);
+    unsigned accw = 0u;
+    unsigned long long my_acc[2] = {0ull, 0ull}, my_prop[2] = {0ull, 0ull}, my_nf = 0ull;
+#pragma unroll
+    for (int a = 0; a < D; ++a) xr[a] = sgr[a] = gr[a] = xh[a] = gh[a] = R(0);
+    if (own) {
+        const R* Fc = (const R*)c.F[sh.fidx];
+        const R* I = (const R*)c.I;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            xr[a] = X[a * c.ldx + n];
+            sgr[a] = sig[a * c.ldx + n];
+            gr[a] = cached ? Fc[a * c.ldf + n] : R(0);
+            sh.xs[a][i] = xr[a];
+            sh.gs[a][i] = gr[a];
+        }
+        if (n >= 1) yv = ((const R*)c.y)[n];
+        if (cached) drive = I[drive_index(c, n)];
+        if (has_next && trap) drive1 = I[drive_index(c, n + 1)];
+        accw = c.acc_win[n];
+    }
     __syncthreads();
+
+    bool odd_flag_wait = false;  // the previous sweep had no parameter barrier
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        const long long s = sh.sweep;
+        const unsigned long long ep = sh.ep0 + (unsigned long long)k + 1ull;
+        if (tid < NP) draw_param_proposal<Model, R, NT>(c, sh, s, tid);
+        const R beta = R(sh.beta);
+        R pr[kMaxP];
+#pragma unroll
+        for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
+
+        // ---- site phases: even sites, then odd sites (Sec. 4.1) ----
+        for (int parity = 0; parity < 2; ++parity) {
+            if (own && (int)(n & 1) == parity) {
+                Nbhd<R, D> nb;
+                R xl[D], gl[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xl[a] = gl[a] = R(0);
+                const R* Fc = (const R*)c.F[sh.fidx];
+                bool ok = true;
+                if (left_halo) {
+                    // the previous tile's last site: final after the last
+                    // parameter barrier, or after its odd flag
+                    if (odd_flag_wait && Sync::tiled) ok = flag_wait(c, 1, b - 1, ep - 1ull);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        gl[a] = __ldcg(Fc + a * c.ldf + n0 - 1);
+                        xl[a] = trap ? __ldcg(X + a * c.ldx + n0 - 1) : R(0);
+                    }
+                }
+                if (right_halo) {
+                    // the next tile's first site (even): final after its even phase
+                    if (Sync::tiled) ok = flag_wait(c, 0, b + 1, ep);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        xh[a] = __ldcg(X + a * c.ldx + n1);
+                        gh[a] = trap ? __ldcg(Fc + a * c.ldf + n1) : R(0);
+                    }
+                }
+                if (!ok) sh.abort = 1;
+                if (n >= 1) {
+                    nb.yn = yv;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        nb.gprev[a] = (i > 0) ? sh.gs[a][i - 1] : gl[a];
+                        nb.xprev[a] = trap ? ((i > 0) ? sh.xs[a][i - 1] : xl[a]) : R(0);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < D; ++a) nb.gcur[a] = gr[a];
+                if (n < M) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        nb.xn1[a] = (i + 1 < T) ? sh.xs[a][i + 1] : xh[a];
+                        nb.gn1[a] = trap ? ((i + 1 < T) ? sh.gs[a][i + 1] : gh[a]) : R(0);
+                    }
+                }
+                R xp[D], gp[D];
+                if (ok && site_core<Model, R>(c, kc, n, s, pr, beta, xr, sgr, drive, nb, xp, gp, my_nf)) {
+                    R* Fw = (R*)c.F[sh.fidx];
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        xr[a] = xp[a];
+                        X[a * c.ldx + n] = xp[a];
+                        sh.xs[a][i] = xp[a];
+                    }
+                    if (cached) {
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            gr[a] = gp[a];
+                            Fw[a * c.ldf + n] = gp[a];
+                            sh.gs[a][i] = gp[a];
+                        }
+                    }
+                    accw += 1u;
+                    my_acc[parity] += 1ull;
+                }
+                my_prop[parity] += 1ull;
+            }
+            __syncthreads();
+            if (sh.abort) goto done;
+            if (Sync::tiled && tid == 0 && parity == 0) flag_post(c, 0, ep);
+        }
+
+        {
+            // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
+            unsigned todo = 0u;
+            for (int l = 0; l < NP; ++l) {
+                if (!((sh.free_mask >> l) & 1u)) continue;
+                if (sh.inbox[l]) todo |= 1u << l;
+            }
+            if (tid == 0)
+                for (int l = 0; l < NP; ++l)
+                    if ((sh.free_mask >> l) & 1u) sh.par_prop[l] += 1ull;
+            // with no parameter barrier this sweep, the neighbours order on
+            // the odd flag posted at its end
+            odd_flag_wait = (todo == 0u);
+            if (!odd_flag_wait) {
+                // operands of the parameter phase: x_{n+1}, g_{n+1}
+                R xn[D], gn[D], f[D], fn[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xn[a] = gn[a] = f[a] = fn[a] = R(0);
+                if (own) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        xn[a] = (i + 1 < T) ? sh.xs[a][i + 1] : xh[a];
+                        gn[a] = (i + 1 < T) ? sh.gs[a][i + 1] : gh[a];
+                    }
+                }
+                // first move: no decision pending
+                int l = __ffs(todo) - 1;
+                R part = R(0);
+                if (own) {
+                    R q[kMaxP];
+#pragma unroll
+                    for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
+                    apply_move<R, NT>(q, sh, l);
+                    move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f, fn);
+                    if (has_next) part = move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta);
+                    if (cached) {
+                        R* Fn = (R*)c.F[sh.fidx ^ 1u];
+#pragma unroll
+                        for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
+                    }
+                }
+                sh.tpart[tslot] = part;
+                __syncthreads();
+                while (true) {
+                    todo &= todo - 1u;
+                    const int l2 = todo ? __ffs(todo) - 1 : -1;
+                    R fA[D], fnA[D], fR[D], fnR[D];
+                    if (tid < 32) {
+                        // warp 0: CTA sum, publish, grid barrier, gather, decide
+                        const unsigned slot = sh.nred & 1u;
+                        const double v = cta_partial<R, NT>(sh.tpart, lane);
+                        if (lane == 0) {
+                            sync.publish(c, slot, v, &sh.cta_total);
+                            if (!sync.arrive_wait(c)) sh.abort = 1;
+                        }
+                        __syncwarp();
+                        if (!sh.abort) {
+                            const double tot = sync.gather(c, slot, lane, &sh.cta_total);
+                            if (lane == 0) decide<R, NT>(sh, l, tot);
+                        }
+                    } else if (own && l2 >= 0) {
+                        // speculation: move l2's values for both outcomes of move l
+                        R qR[kMaxP], qA[kMaxP];
+#pragma unroll
+                        for (int j = 0; j < kMaxP; ++j) qR[j] = pr[j];
+                        apply_move<R, NT>(qR, sh, l2);
+#pragma unroll
+                        for (int j = 0; j < kMaxP; ++j) qA[j] = qR[j];
+                        apply_move<R, NT>(qA, sh, l);
+                        move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, qA, fA, fnA);
+                        move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, qR, fR, fnR);
+                    }
+                    __syncthreads();
+                    if (sh.abort) goto done;
+                    const bool acc = sh.last_acc != 0;
+#pragma unroll
+                    for (int j = 0; j < kMaxP; ++j) pr[j] = sh.q_cur[j];
+                    if (acc) {
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            gr[a] = f[a];
+                            gn[a] = fn[a];
+                        }
+                    }
+                    if (l2 < 0) break;
+                    l = l2;
+                    part = R(0);
+                    if (own) {
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            f[a] = acc ? fA[a] : fR[a];
+                            fn[a] = acc ? fnA[a] : fnR[a];
+                        }
+                        if (has_next) part = move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta);
+                        if (cached) {
+                            R* Fn = (R*)c.F[sh.fidx ^ 1u];
+#pragma unroll
+                            for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
+                        }
+                    }
+                    sh.tpart[tslot] = part;
+                    __syncthreads();
+                }
+                if (own) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) sh.gs[a][i] = gr[a];
+                }
+            }
+        }
+        __syncthreads();
+
+        {
+            // ---- path statistics (Sec. 4.1): after N_init, every N_skip sweeps ----
+            // (the residual of the tile's last site reads the next tile's first
+            // site: a barrier keeps it unchanged until every CTA has recorded)
+            const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
+            if (record) {
+                record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
+                if (!sync.barrier(c, &sh.abort)) goto done;
+            }
+
+            // ---- step-size adaptation during burn-in (Sec. 4.2) ----
+            if (s < c.n_init && ((s + 1) % c.n_skip == 0)) {
+                if (own) {
+                    const double fac = 1.0 + c.alpha * ((double)accw / (double)c.n_skip - c.f_acc);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) sgr[a] = R((double)sgr[a] * fac);
+                    accw = 0u;
+                }
+                if (tid == 0) adapt_params<NP>(c, sh);
+            }
+            end_sweep<NP>(c, sh, s, record, sync);
+            if (Sync::tiled && odd_flag_wait && tid == 0) flag_post(c, 1, ep);
+        }
+    }
+
+done:
+    if (own) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) sig[a * c.ldx + n] = sgr[a];
+        c.acc_win[n] = accw;
+    }
+    store_chain_state(c, sh, sync, my_acc, my_prop, my_nf);
+}
+
+template <class Model, class R, int NT, class Sync>
+__device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
+                            const Sync& sync)
+{
+    if (threadIdx.x == 0) load_chain_state<Model, R, NT>(c, sh);
+    __syncthreads();
+    sweep_chain_general<Model, R, NT>(c, n0, n1, n_sweeps, sh, sync);
 }
 
 template <class Model, class R>
@@ -532,6 +999,27 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
     const int64_t n0 = (int64_t)blockIdx.x * c.tile;
     const int64_t n1 = min(n0 + c.tile, c.M + 1);
     sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
+}
+
+// Resident form (FP32-mixed): tiles of at most kSweepBlock - 32 sites, even
+// when there are several.  It evaluates two maps per site and parameter move
+// to take them off the critical path, which pays where the sweep is bound by
+// synchronisation latency (FP32 arithmetic at moderate M), not by arithmetic
+// throughput (FP64).
+template <class Model>
+__global__ void __launch_bounds__(kSweepBlock, 1) sweep_resident_kernel(Ctx c, int64_t n_sweeps)
+{
+    __shared__ SweepShared<float, kSweepBlock> sh;
+    const int64_t n0 = (int64_t)blockIdx.x * c.tile;
+    const int64_t n1 = min(n0 + c.tile, c.M + 1);
+    if (threadIdx.x == 0) load_chain_state<Model, float, kSweepBlock>(c, sh);
+    __syncthreads();
+    sweep_chain_resident<Model, float, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
+}
+
+bool resident_fits(int prec, int64_t tile, int grid)
+{
+    return prec == 1 && tile <= kSweepBlock - 32 && (grid == 1 || (tile & 1) == 0);
 }
 
 // Many independent chains in one launch: CTA b runs, one after another, the
@@ -558,33 +1046,49 @@ __global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
     }
 }
 
+template <class Model, class R> struct SweepKernels {
+    static const void* general() { return (const void*)sweep_kernel<Model, R>; }
+    static const void* resident() { return nullptr; }
+};
+template <class Model> struct SweepKernels<Model, float> {
+    static const void* general() { return (const void*)sweep_kernel<Model, float>; }
+    static const void* resident() { return (const void*)sweep_resident_kernel<Model>; }
+};
+
 template <class Model, class R>
-static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s)
+static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s)
 {
     Ctx cc = c;
     int64_t ns = n_sweeps;
     void* args[] = {(void*)&cc, (void*)&ns};
-    return cudaLaunchCooperativeKernel((const void*)sweep_kernel<Model, R>, dim3(grid), dim3(kSweepBlock), args, 0, s);
+    const void* k = (resident && resident_fits(prec_of<R>(), c.tile, grid)) ? SweepKernels<Model, R>::resident()
+                                                                            : SweepKernels<Model, R>::general();
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, 0, s);
 }
 
-template <class Model, class R>
-static int max_grid_t(int device)
+static int max_grid_of(const void* k, int device)
 {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<Model, R>, kSweepBlock, 0) != cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSweepBlock, 0) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     return per_sm * sms;
 }
 
-cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, cudaStream_t s)
+template <class Model, class R>
+static int max_grid_t(int device, int resident)
 {
-    PIMC_DISPATCH(launch_sweep_t, c, n_sweeps, grid, s);
+    const void* k = resident ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
+    return k ? max_grid_of(k, device) : 0;
 }
 
-int sweep_max_grid(int model, int prec, int device)
+cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s)
 {
-    PIMC_DISPATCH(max_grid_t, device);
+    PIMC_DISPATCH(launch_sweep_t, c, n_sweeps, grid, resident, s);
+}
+
+int sweep_max_grid(int model, int prec, int device, int resident)
+{
+    PIMC_DISPATCH(max_grid_t, device, resident);
 }
 
 // ---- batched launch --------------------------------------------------------
