@@ -22,6 +22,14 @@
  *   orc_moments, histograms  pinned: numpy mean/var/histogram of recorded samples
  *   orc_grad, map_vjp        pinned: central finite differences of the action
  *   orc_hmc                  pinned: closed-form linear-Gaussian posterior
+ *   trapezoid scheme,        pinned: closed-form linear-Gaussian posterior of
+ *   uniform proposals        the trapezoid system (T-LG), both proposal laws
+ *   orc_paper_gates, the     pinned: a_inf(V_a) = 1/2 and tau(V_a) = tau0 +
+ *   paper's HH variant       tau1 for each gate (Table 1), a resting state near
+ *                            0 mV, repeated spikes under a 10 uA/cm^2 drive;
+ *                            its map VJP by central differences
+ *   orc_residual_moments,    pinned: numpy over the recorded residuals;
+ *   orc_forecast             deterministic forecast = iterated map, noise law
  *   HH drive hold, initial   parity unpinned against the paper (the paper's own
  *   path, HH constants       example uses tanh rates and a trapezoid rule)
  */
