@@ -2,12 +2,14 @@
 
 Workload: Hodgkin-Huxley D = 4, all 7 parameters free, M = 32768 time steps
 (dt = 0.02 ms), seeded OU drive, noisy voltage observations.  One step is one
-full checkerboard sweep: even sites, odd sites, 7 sequential parameter moves
-(each a full-path RK4 pass plus an FP64 reduction and accept test) and, every
-N_skip = 10 sweeps, the moment/histogram update.  value = (M + 1) site updates
-per sweep / device time per sweep, summed over ranks (independent replica
-chains, weak scaling).  The L2 is flushed (a 256 MiB write) before every timed
-sweep; each sweep is timed with CUDA events on the sampler's stream.
+launch of N_skip = 10 full checkerboard sweeps -- each sweep: even sites, odd
+sites, 7 sequential parameter moves (each a full-path RK4 pass plus an FP64
+reduction and accept test) -- ending with one moment/histogram/residual
+record, so that a step runs every row of the hot path once.  value =
+(M + 1) * N_skip site updates per step / device time per step, summed over
+ranks (independent replica chains, weak scaling).  The L2 is flushed (a
+256 MiB write) before every timed step; each step is timed with CUDA events on
+the sampler's stream.
 
 --impl reference times the serial FP64 CPU oracle (the method's plain
 statement) on the host for the same workload and metric.
@@ -33,6 +35,7 @@ UNIT = "site-updates/s"
 M_DEFAULT = 32768
 NSKIP = 10
 SEED = 1
+REF_BUDGET_S = 120.0
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations + stage combinations):
@@ -126,6 +129,10 @@ def cpu_baseline(prob, budget_s=12.0):
 
 
 def run_reference(args):
+    """The serial FP64 oracle on one host core, same workload, metric and unit.
+    Each step is a bounded sample of the workload: one full sweep (a tenth of
+    the GPU arm's step); the timed steps stop after REF_BUDGET_S seconds so the
+    run ends within a few minutes whatever K is."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -140,33 +147,41 @@ def run_reference(args):
     for _ in range(args.warmup):
         ch.sweep(1, SEED)
     times = []
+    t_start = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
         ch.sweep(1, SEED)
         times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > REF_BUDGET_S:
+            break
     tot = sum(times)
-    value = (prob.M + 1) * args.steps / tot
+    n = len(times)
+    value = (prob.M + 1) * n / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * tot / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": 7,
-                                            "sweeps_per_step": 1, "l2": "host"},
+                                            "sweeps_per_step": 1, "l2": "host",
+                                            "steps_requested": args.steps},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full sweeps, serial FP64 oracle"},
+                             "sample": f"{n} full sweeps of the M={args.M} workload (of {args.steps} requested, "
+                                       f"bounded at {REF_BUDGET_S:.0f} s), serial FP64 oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def run_profile_case(args):
-    """Three single-sweep launches of the sweep kernel in each precision on the
-    bench workload (no timing); the case the ncu captures use."""
+    """Three launches of one bench step (N_skip sweeps) of the sweep kernel in
+    each precision on the bench workload (no timing); the case the ncu
+    captures use."""
     from paper_1103_4887_gb300 import pimc, synth
     prob = synth.hh_problem(args.M, data_seed=0, free="all")
     for prec in (pimc.FP32_MIXED, pimc.FP64):
         s = pimc.Sampler.from_problem(prob, precision=prec)
         s.set_schedule(n_init=0, n_skip=NSKIP)
         for _ in range(3):
-            s.sweep(1, SEED)
+            s.sweep(NSKIP, SEED)
+        print(json.dumps({"precision": prec, "form": s.sweep_form(), "grid_block": list(s.launch_info())}))
         s.close()
     print("profile case done")
 
@@ -212,17 +227,27 @@ def run_sweep_M(args):
                          "rk4_maps_per_s": maps / (ms * 1e-3), "achieved_tflops": tf, "roofline_frac": tf / peak,
                          "grid_block": list(s.launch_info())}
             s.close()
-        ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
-        ch.set_data(prob.y, prob.I)
-        ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
-        ch.set_steps(prob.sig_x, prob.sig_p)
         n_cpu = 100 if M <= 1 << 12 else (10 if M <= 1 << 16 else 2)
-        t0 = time.perf_counter()
-        ch.sweep(n_cpu, SEED)
-        cpu_s = (time.perf_counter() - t0) / n_cpu
-        row["oracle_1core"] = {"s_per_sweep": cpu_s, "site_updates_per_s": (M + 1) / cpu_s, "sweeps_timed": n_cpu}
+        for key, omp in (("oracle_1core", False), ("oracle_allcores", True)):
+            try:
+                ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf, openmp=omp)
+            except Exception as e:  # no OpenMP build on this host
+                row[key] = {"error": repr(e)}
+                continue
+            ch.set_data(prob.y, prob.I)
+            ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+            ch.set_steps(prob.sig_x, prob.sig_p)
+            t0 = time.perf_counter()
+            ch.sweep(n_cpu, SEED)
+            cpu_s = (time.perf_counter() - t0) / n_cpu
+            row[key] = {"s_per_sweep": cpu_s, "site_updates_per_s": (M + 1) / cpu_s, "sweeps_timed": n_cpu,
+                        "threads": oracle.threads(omp)}
+        cpu_s = row["oracle_1core"]["s_per_sweep"]
         row["speedup_fp32_vs_oracle"] = cpu_s / (row["fp32mixed"]["ms_per_sweep"] * 1e-3)
         row["speedup_fp64_vs_oracle"] = cpu_s / (row["fp64"]["ms_per_sweep"] * 1e-3)
+        if "s_per_sweep" in row["oracle_allcores"]:
+            row["speedup_fp32_vs_oracle_allcores"] = (row["oracle_allcores"]["s_per_sweep"]
+                                                      / (row["fp32mixed"]["ms_per_sweep"] * 1e-3))
         print(json.dumps(row), flush=True)
 
 
@@ -292,6 +317,86 @@ def run_paper(args):
         out[name] = {"ms_per_sweep": ms, "site_updates_per_s": 8001 / (ms * 1e-3),
                      "seconds_per_1e6_sweeps": ms * 1e3, "vs_paper_gtx460_683s": 683.0 / (ms * 1e3)}
         s.close()
+    return out
+
+
+def run_mixed(args):
+    """FP32-mixed against plain FP64 on the bench workload (HH, M = 32768, all 7
+    parameters free): (1) per-site Delta A error on the same path and
+    proposals; (2) accept-flip rate -- the fraction of site decisions of one
+    sweep from the same state, seed and counters that differ; (3) shift of the
+    posterior parameter means in Monte Carlo standard errors (batch means of
+    the parameter traces), both chains from the true path after a burn-in."""
+    import torch
+    from paper_1103_4887_gb300 import diagnostics, pimc, synth
+    M = args.M
+    prob = synth.hh_problem(M, data_seed=0, free="all")
+    out = {"M": M, "n_free": 7}
+    st = torch.cuda.current_stream()
+    # (1) Delta A on the same states and proposals
+    X = synth.random_path_near(prob, prob.X_true, 0.5 * prob.sig_x, seed=11)
+    Xp = synth.random_path_near(prob, X, 2.0 * prob.sig_x, seed=12)
+    d = {}
+    for name, prec in (("fp64", pimc.FP64), ("fp32", pimc.FP32_MIXED)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_path(X)
+        d[name] = s.site_delta(Xp)
+        s.close()
+    err = np.abs(d["fp32"] - d["fp64"])
+    big = np.abs(d["fp64"]) > 1.0
+    out["delta_A"] = {"abs_err_median": float(np.median(err)), "abs_err_p99": float(np.quantile(err, 0.99)),
+                      "abs_err_max": float(err.max()),
+                      "rel_err_median_where_abs_dA_gt_1": float(np.median(err[big] / np.abs(d["fp64"][big]))),
+                      "rel_err_p99_where_abs_dA_gt_1": float(np.quantile(err[big] / np.abs(d["fp64"][big]), 0.99)),
+                      "sites": int(M + 1)}
+    # (2) accept flips: one sweep from the same state (path near the truth, adapted steps)
+    base = pimc.Sampler.from_problem(prob, precision=pimc.FP64)
+    base.set_schedule(n_init=200, n_skip=20, f_acc=0.4, alpha=0.5)
+    base.sweep(200, SEED)
+    X0, p0 = base.state()
+    sx, sp = base.steps()
+    base.close()
+    moved = {}
+    for name, prec in (("fp64", pimc.FP64), ("fp32", pimc.FP32_MIXED)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_params(p0, prob.lo, prob.hi, prob.free)
+        s.set_path(X0)
+        s.set_steps(sx, sp)
+        s.set_schedule(n_init=10 ** 9, n_skip=10 ** 6)
+        flips_site, flips_par = [], []
+        res = []
+        for k in range(5):
+            s.set_path(X0)
+            s.set_params(p0, prob.lo, prob.hi, prob.free)
+            s.sweep(1, SEED + k)
+            X1, p1 = s.state()
+            res.append((np.any(X1 != X0, axis=0), p1 != p0))
+        moved[name] = res
+        s.close()
+    fs = sum(int(np.sum(a[0] != b[0])) for a, b in zip(moved["fp64"], moved["fp32"]))
+    fp_ = sum(int(np.sum(a[1] != b[1])) for a, b in zip(moved["fp64"], moved["fp32"]))
+    out["accept_flips"] = {"site_flips": fs, "site_decisions": 5 * (M + 1), "site_flip_rate": fs / (5 * (M + 1)),
+                           "param_flips": fp_, "param_decisions": 5 * 7}
+    # (3) posterior parameter means
+    tr = {}
+    for name, prec, n in (("fp64", pimc.FP64, 8000), ("fp32", pimc.FP32_MIXED, 8000)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
+        s.set_path(prob.X_true)
+        s.set_stream(st.cuda_stream)
+        s.set_schedule(n_init=2000, n_skip=20, f_acc=0.4, alpha=0.5)
+        s.sweep(2000, SEED, sync=False)
+        s.set_param_trace(n)
+        s.sweep(n, SEED, sync=False)
+        s.sync()
+        tr[name] = s.param_trace()
+        s.close()
+    m64, m32 = tr["fp64"].mean(0), tr["fp32"].mean(0)
+    se64, se32 = diagnostics.batch_means_se(tr["fp64"], 20), diagnostics.batch_means_se(tr["fp32"], 20)
+    z = np.abs(m32 - m64) / np.sqrt(se64 ** 2 + se32 ** 2 + 1e-300)
+    out["posterior_mean_shift"] = {"sweeps_each": 8000, "burn_in": 2000, "mean_fp64": m64.tolist(),
+                                   "mean_fp32": m32.tolist(), "shift_in_se": z.tolist(),
+                                   "max_shift_in_se": float(z.max())}
     return out
 
 
@@ -381,6 +486,9 @@ def main():
     ap.add_argument("--paper", action="store_true",
                     help="the paper's own setting: HH variant with tanh kinetics, trapezoid rule, uniform "
                          "proposals, M = 8000 at 25 kHz, all 7 parameters free")
+    ap.add_argument("--mixed", action="store_true",
+                    help="FP32-mixed vs FP64 on the bench workload: Delta A error, accept-flip rate, "
+                         "posterior-mean shift in MC standard errors")
     ap.add_argument("--ess", action="store_true",
                     help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
     args = ap.parse_args()
@@ -396,6 +504,9 @@ def main():
         return
     if args.ess:
         print(json.dumps(run_ess(args)), flush=True)
+        return
+    if args.mixed:
+        print(json.dumps(run_mixed(args)), flush=True)
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
@@ -424,7 +535,7 @@ def main():
         s = pimc.Sampler.from_problem(prob, precision=precision)
         s.set_stream(stream.cuda_stream)
         s.set_chain(rank)
-        s.set_schedule(n_init=args.warmup, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
+        s.set_schedule(n_init=args.warmup * NSKIP, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
         return s
 
     samp = make(prec)
@@ -432,7 +543,7 @@ def main():
 
     def timed_steps(s, K, warm):
         for _ in range(warm):
-            s.sweep(1, SEED, sync=False)
+            s.sweep(NSKIP, SEED, sync=False)
         torch.cuda.synchronize()
         s.sync()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -442,7 +553,7 @@ def main():
         for e0, e1 in evs:
             flush.zero_()
             e0.record(stream)
-            s.sweep(1, SEED, sync=False)
+            s.sweep(NSKIP, SEED, sync=False)
             e1.record(stream)
         torch.cuda.synchronize()
         if dist is not None:
@@ -459,7 +570,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     sites = prob.M + 1
-    value = world * sites * args.steps / (total_ms * 1e-3)
+    value = world * sites * NSKIP * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
 
     # steady state: one persistent launch of many sweeps, no flush in between
@@ -483,11 +594,11 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         samp.load_data(y_pin.data_ptr(), I_pin.data_ptr())
-        samp.sweep(1, SEED, sync=False)
+        samp.sweep(NSKIP, SEED, sync=False)
         p_now = samp.params()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * sites * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": world * sites * NSKIP * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (2 * prob.M + 1), "d2h_bytes_per_step": 8 * 7}
 
     # FP64 form on the same workload (for the FP32-mixed vs FP64 comparison)
@@ -495,10 +606,12 @@ def main():
     if prec == pimc.FP32_MIXED and args.fp64_steps > 0:
         s64 = make(pimc.FP64)
         ms64 = timed_steps(s64, args.fp64_steps, 3)
-        fp64 = {"value": world * sites * args.fp64_steps / (sum(ms64) * 1e-3), "ms_per_step": sum(ms64) / len(ms64)}
+        fp64 = {"value": world * sites * NSKIP * args.fp64_steps / (sum(ms64) * 1e-3),
+                "ms_per_step": sum(ms64) / len(ms64)}
         s64.close()
 
     grid_block = list(samp.launch_info())
+    form = samp.sweep_form()
     peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -510,10 +623,11 @@ def main():
         peak_tflops = FLOP_PER_MAP / t_map / 1e12
     else:
         peak_tflops = 1.25  # nominal FP64 rate of the part
-    achieved = maps * FLOP_PER_MAP / (ms_per_step * 1e-3) / 1e12
+    achieved = maps * NSKIP * FLOP_PER_MAP / (ms_per_step * 1e-3) / 1e12
+    kname = "sweep_resident_kernel<HH>" if form == "resident" else "sweep_kernel<HH>"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": None,
-            "kernel": "sweep_kernel<HH>", "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
+            "kernel": kname, "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -526,6 +640,10 @@ def main():
         except Exception as e:  # reported, not hidden
             extras["batch"] = {"error": repr(e)}
         try:
+            extras["mixed"] = run_mixed(args)
+        except Exception as e:
+            extras["mixed"] = {"error": repr(e)}
+        try:
             ess = run_ess(args)
             extras["ess"] = {k: ({kk: v[kk] for kk in ("min_ess_per_s", "median_ess_per_s", "seconds")}
                                  if isinstance(v, dict) else v) for k, v in ess.items()}
@@ -537,9 +655,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == pimc.FP32_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": n_free,
-                           "precision": args.precision, "sweeps_per_step": 1, "n_skip": NSKIP,
-                           "l2": "flushed (256 MiB write) before every timed sweep",
-                           "grid_block": grid_block},
+                           "precision": args.precision, "sweeps_per_step": NSKIP, "n_skip": NSKIP,
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "grid_block": grid_block, "form": form},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk.rows),
                 "steady_state": steady, "fp64": fp64}

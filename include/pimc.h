@@ -266,6 +266,17 @@ int pimc_accept_stats(pimc_t h, uint64_t* site_acc, uint64_t* site_prop, uint64_
                       uint64_t* par_prop);
 /* Launch geometry chosen for the sweep kernel (grid CTAs, threads per CTA). */
 int pimc_launch_info(pimc_t h, int* grid, int* block);
+/* Form the sweep takes at the current size, precision and grid: *resident = 1
+ * when every site lives in one thread for the whole launch (FP32-mixed, at
+ * most 224 sites per CTA; the site phases then order on flags between
+ * neighbouring CTAs), 0 for the general form (threads stride over the tile).
+ * Both forms give the same bits for the same tiles. */
+int pimc_sweep_form(pimc_t h, int* resident);
+/* Which forms the sweep may take: PIMC_FORM_AUTO (default; the resident form
+ * where it fits) or PIMC_FORM_GENERAL (always the general form, e.g. to
+ * compare the two).  PIMC_ERR_ARG for other values. */
+typedef enum { PIMC_FORM_AUTO = 0, PIMC_FORM_GENERAL = 1 } pimc_form;
+int pimc_set_sweep_form(pimc_t h, int form);
 
 /* ---- batched launch: many chains and data sets of uneven M ----------------- */
 

@@ -38,6 +38,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 4
 #define ORC_MAXP 8
@@ -586,6 +589,16 @@ int orc_set_sweep_counter(orc_state* s, int64_t sweep, double beta)
     s->sweep = sweep; s->beta = beta; return 0;
 }
 
+/* Threads an OpenMP build uses (1 for the serial build). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ---- action ------------------------------------------------------------ */
 /* A_o = 1/2 sum_{n=1}^M Rm (x_{n,0} - y_n)^2;  A_f = 1/2 sum_{n=0}^{M-1} sum_a Rf_a eps_{n+1,a}^2
  * (Sec. 2.1), eps from the explicit RK4 map or the trapezoid rule. */
@@ -671,12 +684,17 @@ static double orc_param_delta_cache(const orc_state* s, const double* pn, double
 {
     int64_t nc = orc_cache_len(s);
     double* g = gnew ? gnew : (double*)malloc(sizeof(double) * (size_t)(s->D * (s->M + 1)));
-    double x[ORC_MAXD], gv[ORC_MAXD], dA = 0.0, sc = 0.0;
+    double dA = 0.0, sc = 0.0;
+    /* (the OpenMP build, timing only, splits both loops over threads; its sum
+     * order then differs from this serial order) */
+#pragma omp parallel for schedule(static)
     for (int64_t n = 0; n < nc; ++n) {
+        double x[ORC_MAXD], gv[ORC_MAXD];
         orc_load_site(s, n, x);
         orc_cache_value(s, x, pn, n, gv);
         for (int a = 0; a < s->D; ++a) g[(int64_t)a * (s->M + 1) + n] = gv[a];
     }
+#pragma omp parallel for schedule(static) reduction(+ : dA, sc)
     for (int64_t n = 0; n < s->M; ++n) {
         for (int a = 0; a < s->D; ++a) {
             double g1o = s->scheme == ORC_SCHEME_RK4 ? 0.0 : FI(s, a, n + 1);
@@ -847,6 +865,7 @@ int orc_site_update(orc_state* s, int64_t n, const double* z, double u)
         xp[a] = x[a] + s->sig[(int64_t)a * (s->M + 1) + n] * z[a];
         if (!(xp[a] >= s->xlo[a] && xp[a] <= s->xhi[a])) inside = 0;
     }
+#pragma omp atomic
     s->site_prop[parity] += 1;
     s->site_margin[n] = INFINITY;
     if (!inside) return 0;
@@ -859,6 +878,7 @@ int orc_site_update(orc_state* s, int64_t n, const double* z, double u)
         for (int a = 0; a < s->D; ++a) XI(s, a, n) = xp[a];
         if (cached) for (int a = 0; a < s->D; ++a) FI(s, a, n) = fp[a];
         s->acc_win[n] += 1;
+#pragma omp atomic
         s->site_acc[parity] += 1;
     }
     return acc;
@@ -880,10 +900,14 @@ static void orc_site_uniform_draws(uint64_t seed, uint32_t chain, uint64_t sweep
     *u = orc_u01(w[0], w[1]);
 }
 
+/* The sites of one parity are independent given the other parity, so the
+ * OpenMP build (timing only; the test build is serial) may move them in
+ * parallel. */
 static void orc_site_phase(orc_state* s, int parity, uint64_t seed)
 {
-    double z[ORC_MAXD], u;
+#pragma omp parallel for schedule(static)
     for (int64_t n = parity; n <= s->M; n += 2) {
+        double z[ORC_MAXD], u;
         if (s->proposal == ORC_PROPOSAL_UNIFORM) orc_site_uniform_draws(seed, s->chain, (uint64_t)s->sweep, n, s->D, z, &u);
         else orc_site_draws(seed, s->chain, (uint64_t)s->sweep, n, s->D, z, &u);
         orc_site_update(s, n, z, u);

@@ -119,6 +119,10 @@ int  orc_set_histograms(orc_state* s, int n_sel, const int64_t* comp, const doub
                         const double* hi, int n_bins);
 void orc_histograms(const orc_state* s, uint64_t* counts);
 
+/* Threads of an OpenMP build (liboracle_omp: timing only, its parameter sums
+ * add in another order); 1 for the serial test build. */
+int  orc_threads(void);
+
 /* Whole-path Hybrid Monte Carlo trajectory (X and free p move together). */
 int  orc_hmc(orc_state* s, int64_t n_traj, int n_leap, double eps, const double* inv_mass,
              uint64_t seed, int64_t* n_acc);

@@ -38,6 +38,7 @@ struct pimc_handle_s {
     unsigned long long* flags = nullptr;  // neighbour epoch flags [2][kMaxGrid] of the sweep kernel
     uint64_t epoch = 0;                   // sweeps launched so far: the flags' epoch base
     bool resident = false;                // the sweep takes the resident form (one site a thread)
+    int form = PIMC_FORM_AUTO;            // forms the sweep may take
     unsigned* ticket = nullptr;
     double* red = nullptr;
     double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
@@ -213,7 +214,7 @@ void choose_grid(pimc_t h)
     // tile's halo sites change in fixed phases of the sweep
     if (g > 1) h->tile += h->tile & 1;
     h->grid = (int)((sites + h->tile - 1) / h->tile);
-    h->resident = resident_fits(h->prec, h->tile, h->grid) &&
+    h->resident = h->form == PIMC_FORM_AUTO && resident_fits(h->prec, h->tile, h->grid) &&
                   h->grid <= sweep_max_grid(h->model, h->prec, h->device, 1);
 }
 
@@ -917,6 +918,22 @@ int pimc_launch_info(pimc_t h, int* grid, int* block)
     if (!h) return PIMC_ERR_ARG;
     if (grid) *grid = h->grid;
     if (block) *block = kSweepBlock;
+    return PIMC_OK;
+}
+
+int pimc_sweep_form(pimc_t h, int* resident)
+{
+    if (!h || !resident) return PIMC_ERR_ARG;
+    *resident = h->resident ? 1 : 0;
+    return PIMC_OK;
+}
+
+int pimc_set_sweep_form(pimc_t h, int form)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (form != PIMC_FORM_AUTO && form != PIMC_FORM_GENERAL) return fail(h, PIMC_ERR_ARG, "unknown sweep form %d", form);
+    h->form = form;
+    choose_grid(h);
     return PIMC_OK;
 }
 

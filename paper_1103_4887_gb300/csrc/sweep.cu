@@ -45,6 +45,7 @@ template <class R, int NT> struct SweepShared {
     R xs[kMaxD][NT];                // resident form: x of site n0 + i at [a][i]
     R gs[kMaxD][NT];                // resident form: cached value of site n0 + i at [a][i]
     double cta_total;               // CTA sum of a parameter move (CTA-local chains)
+    double wsum[4];                 // warp sums of a parameter move's CTA partial
     unsigned long long ep0;         // resident form: epoch base of the neighbour flags
     int abort;
     int last_acc;                   // outcome of the latest parameter decision
@@ -358,20 +359,24 @@ __device__ __forceinline__ double block_sum(double v, double* wsum)
     return t;
 }
 
-// Warp 0: FP64 sum of the NT per-thread partials of a parameter move, from the
-// per-thread values up (pairwise within a lane, then across lanes); valid in
-// lane 0.
+// FP64 sum of the NT per-thread partials of a parameter move, from the
+// per-thread values up, by warps 0..3 (spread over the SM's four schedulers,
+// whose FP64 issue is slow): warp q adds entries [q NT/4, (q+1) NT/4) per lane
+// in index order, then across lanes; the four warp sums meet in shared memory
+// after a named barrier of threads 0..127.  Called by threads 0..127 (a CTA
+// barrier after the partials were written); valid in all of them.
 template <class R, int NT>
-__device__ __forceinline__ double cta_partial(const R* tpart, int lane)
+__device__ __forceinline__ double cta_partial(const R* tpart, double* wsum)
 {
-    double t[NT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, q = tid >> 5;
+    constexpr int kPer = NT / 128;
+    double v = (double)tpart[q * (NT / 4) + lane];
 #pragma unroll
-    for (int q = 0; q < NT / 32; ++q) t[q] = (double)tpart[lane + 32 * q];
-#pragma unroll
-    for (int w = NT / 64; w >= 1; w >>= 1)
-#pragma unroll
-        for (int q = 0; q < w; ++q) t[q] += t[q + w];
-    return warp_sum(t[0]);
+    for (int k = 1; k < kPer; ++k) v += (double)tpart[q * (NT / 4) + lane + 32 * k];
+    v = warp_sum(v);
+    if (lane == 0) wsum[q] = v;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    return (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
 }
 
 // Synchronisation policies of a chain's sweep.  GridSync: the chain is tiled
@@ -388,24 +393,24 @@ struct GridSync {
         c.partials[slot * kMaxGrid + blockIdx.x] = v;
     }
     // Warp-wide: every lane loads its CTAs' partials (independent loads, one
-    // L2 round trip), then a fixed-order sum; valid in every lane.
+    // L2 round trip), adds them in index order (only the groups that exist:
+    // each FP64 add costs many issue cycles), then across lanes; valid in
+    // every lane.
     __device__ __forceinline__ double gather(const Ctx& c, unsigned slot, int lane, const double*) const
     {
         const int G = (int)gridDim.x;
         const double* part = c.partials + slot * kMaxGrid;
         double v = 0.0;
-        for (int base = 0; base < G; base += 512) {
-            double t[16];
+        for (int base = 0; base < G; base += 256) {
+            double t[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 8; ++j) {
                 const int i = base + lane + 32 * j;
                 t[j] = (i < G) ? __ldcg(part + i) : 0.0;
             }
 #pragma unroll
-            for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                for (int j = 0; j < w; ++j) t[j] += t[j + w];
-            v += t[0];
+            for (int j = 0; j < 8; ++j)
+                if (base + 32 * j < G) v += t[j];
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -465,17 +470,19 @@ __device__ __forceinline__ void draw_param_proposal(const Ctx& c, SweepShared<R,
     sh.elog[l] = -log(u01d(w.x, w.y));
     sh.inbox[l] = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
     double pv[kMaxP];
-    for (int q = 0; q < kMaxP; ++q) pv[q] = sh.p[q];
-    pv[l] = pl;
+#pragma unroll
+    for (int q = 0; q < kMaxP; ++q) pv[q] = (q == l) ? pl : sh.p[q];
     Model::prep(pv, sh.q_new[l]);
 }
 
-// The model-parameter vector of move l applied to q.
+// The model-parameter vector of move l applied to q (components l, and 7
+// with l = 6).  Static indices keep q in registers.
 template <class R, int NT>
 __device__ __forceinline__ void apply_move(R* q, const SweepShared<R, NT>& sh, int l)
 {
-    q[l] = sh.q_new[l][l];
-    if (l == 6) q[7] = sh.q_new[6][7];
+#pragma unroll
+    for (int j = 0; j < kMaxP; ++j)
+        if (j == l || (j == 7 && l == 6)) q[j] = sh.q_new[l][j];
 }
 
 // Decision of move l on the total change of action v: Eq. (Paccept) as
@@ -581,6 +588,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
         for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
 
         // ---- even then odd sites (Sec. 4.1) ----
+#pragma unroll
         for (int parity = 0; parity < 2; ++parity) {
             R* Fc = (R*)c.F[sh.fidx];
             const int64_t first = n0 + (((n0 & 1) != parity) ? 1 : 0);
@@ -627,8 +635,8 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             sh.tpart[tid] = part;
             __syncthreads();
             const unsigned slot = sh.nred & 1u;
-            if (tid < 32) {
-                const double v = cta_partial<R, NT>(sh.tpart, tid);
+            if (tid < 128) {
+                const double v = cta_partial<R, NT>(sh.tpart, sh.wsum);
                 if (tid == 0) sync.publish(c, slot, v, &sh.cta_total);
             }
             if (!sync.barrier(c, &sh.abort)) goto done;
@@ -766,6 +774,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
         for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
 
         // ---- site phases: even sites, then odd sites (Sec. 4.1) ----
+#pragma unroll
         for (int parity = 0; parity < 2; ++parity) {
             if (own && (int)(n & 1) == parity) {
                 Nbhd<R, D> nb;
@@ -885,10 +894,11 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     todo &= todo - 1u;
                     const int l2 = todo ? __ffs(todo) - 1 : -1;
                     R fA[D], fnA[D], fR[D], fnR[D];
+                    const unsigned slot = sh.nred & 1u;
+                    double v = 0.0;
+                    if (tid < 128) v = cta_partial<R, NT>(sh.tpart, sh.wsum);
                     if (tid < 32) {
-                        // warp 0: CTA sum, publish, grid barrier, gather, decide
-                        const unsigned slot = sh.nred & 1u;
-                        const double v = cta_partial<R, NT>(sh.tpart, lane);
+                        // warp 0: publish, grid barrier, gather, decide
                         if (lane == 0) {
                             sync.publish(c, slot, v, &sh.cta_total);
                             if (!sync.arrive_wait(c)) sh.abort = 1;
@@ -899,16 +909,30 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                             if (lane == 0) decide<R, NT>(sh, l, tot);
                         }
                     } else if (own && l2 >= 0) {
-                        // speculation: move l2's values for both outcomes of move l
-                        R qR[kMaxP], qA[kMaxP];
+                        // speculation: move l2's values for both outcomes of
+                        // move l, one map instance evaluated twice (two inlined
+                        // copies would share subexpressions, and the compiler
+                        // would fuse multiply-adds differently from the
+                        // general form's single map)
+#pragma unroll 1
+                        for (int o = 0; o < 2; ++o) {
+                            R q[kMaxP], f2[D], fn2[D];
 #pragma unroll
-                        for (int j = 0; j < kMaxP; ++j) qR[j] = pr[j];
-                        apply_move<R, NT>(qR, sh, l2);
+                            for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
+                            apply_move<R, NT>(q, sh, l2);
+                            if (o == 1) apply_move<R, NT>(q, sh, l);
+                            move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f2, fn2);
 #pragma unroll
-                        for (int j = 0; j < kMaxP; ++j) qA[j] = qR[j];
-                        apply_move<R, NT>(qA, sh, l);
-                        move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, qA, fA, fnA);
-                        move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, qR, fR, fnR);
+                            for (int a = 0; a < D; ++a) {
+                                if (o == 1) {
+                                    fA[a] = f2[a];
+                                    fnA[a] = fn2[a];
+                                } else {
+                                    fR[a] = f2[a];
+                                    fnR[a] = fn2[a];
+                                }
+                            }
+                        }
                     }
                     __syncthreads();
                     if (sh.abort) goto done;

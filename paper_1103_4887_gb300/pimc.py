@@ -34,7 +34,7 @@ EXPORTS = [
     "pimc_set_chain", "pimc_sweep", "pimc_hmc", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
-    "pimc_launch_info", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
+    "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
     "pimc_debug_skip_arrive", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
     "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
@@ -108,6 +108,8 @@ def _declare(L):
         "pimc_get_sweep": [_vp, _vp, _vp],
         "pimc_accept_stats": [_vp, _vp, _vp, _vp, _vp],
         "pimc_launch_info": [_vp, _vp, _vp],
+        "pimc_sweep_form": [_vp, _vp],
+        "pimc_set_sweep_form": [_vp, _int],
         "pimc_residual_moments": [_vp, _vp, _vp, _vp],
         "pimc_forecast": [_vp, _i64, _vp, _int, _int, ctypes.c_uint64, _vp],
         "pimc_checkpoint_save": [_vp, ctypes.c_char_p],
@@ -372,6 +374,16 @@ class Sampler:
         b = ctypes.c_int()
         self._ck(self._L.pimc_launch_info(self._h, ctypes.byref(g), ctypes.byref(b)))
         return g.value, b.value
+
+    def set_sweep_form(self, form):
+        """'auto' (the resident form where it fits) or 'general'."""
+        self._ck(self._L.pimc_set_sweep_form(self._h, {"auto": 0, "general": 1}.get(form, -1)))
+
+    def sweep_form(self):
+        """'resident' (one site a thread for the whole launch) or 'general'."""
+        r = ctypes.c_int()
+        self._ck(self._L.pimc_sweep_form(self._h, ctypes.byref(r)))
+        return "resident" if r.value else "general"
 
     def checkpoint_save(self, path):
         self._ck(self._L.pimc_checkpoint_save(self._h, os.fsencode(path)))
