@@ -368,9 +368,10 @@ def run_mixed(args):
         for k in range(5):
             s.set_path(X0)
             s.set_params(p0, prob.lo, prob.hi, prob.free)
+            Xb, pb = s.state()  # as stored (FP32-mixed rounds the path)
             s.sweep(1, SEED + k)
             X1, p1 = s.state()
-            res.append((np.any(X1 != X0, axis=0), p1 != p0))
+            res.append((np.any(X1 != Xb, axis=0), p1 != pb))
         moved[name] = res
         s.close()
     fs = sum(int(np.sum(a[0] != b[0])) for a, b in zip(moved["fp64"], moved["fp32"]))
@@ -421,8 +422,8 @@ def run_ess(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 20000),
-                                ("metropolis_fp64", pimc.FP64, 2000, 4000)):
+    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 100000),
+                                ("metropolis_fp64", pimc.FP64, 2000, 16000)):
         s = pimc.Sampler.from_problem(prob, precision=prec)
         s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
         s.set_path(prob.X_true)
@@ -452,7 +453,7 @@ def run_ess(args):
     for _ in range(12):
         acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
         eps *= float(np.exp(1.5 * (acc - 0.7)))
-    n_traj = 1500
+    n_traj = 2500
     s.set_param_trace(n_traj)
     acc_box = {}
     secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
