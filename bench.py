@@ -440,29 +440,29 @@ def run_ess(args):
         s.close()
 
     # whole-path HMC: diagonal mass from burn-in variances, step tuned to ~70 %
-    s = pimc.Sampler.from_problem(prob, precision=pimc.FP64)
-    s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
-    s.set_path(prob.X_true)
-    s.set_stream(st.cuda_stream)
-    s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
-    s.sweep(4000, SEED, sync=False)
-    mean, var, J = s.moments()
-    inv_mass = np.where(np.isfinite(var) & (var > 0), var, 1e-12)
-    s.set_schedule(n_init=10 ** 9, n_skip=1)
-    eps, n_leap = 0.05, 20
-    for _ in range(12):
-        acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
-        eps *= float(np.exp(1.5 * (acc - 0.7)))
-    n_traj = 2500
-    s.set_param_trace(n_traj)
-    acc_box = {}
-    secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
-    tr = s.param_trace()
-    ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
-    out["hmc_fp64"] = {"trajectories": n_traj, "n_leap": n_leap, "eps": eps, "accept": acc_box["n"] / n_traj,
-                       "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
-                       "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
-    s.close()
+    for name, prec, n_traj in (("hmc_fp64", pimc.FP64, 2500), ("hmc_fp32mixed", pimc.FP32_MIXED, 10000)):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
+        s.set_path(prob.X_true)
+        s.set_stream(st.cuda_stream)
+        s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
+        s.sweep(4000, SEED, sync=False)
+        mean, var, J = s.moments()
+        inv_mass = np.where(np.isfinite(var) & (var > 0), var, 1e-12)
+        s.set_schedule(n_init=10 ** 9, n_skip=1)
+        eps, n_leap = 0.05, 20
+        for _ in range(12):
+            acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
+            eps *= float(np.exp(1.5 * (acc - 0.7)))
+        s.set_param_trace(n_traj)
+        acc_box = {}
+        secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
+        tr = s.param_trace()
+        ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
+        out[name] = {"trajectories": n_traj, "n_leap": n_leap, "eps": eps, "accept": acc_box["n"] / n_traj,
+                     "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
+                     "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
+        s.close()
     return out
 
 

@@ -47,6 +47,7 @@ template <class R, int NT> struct SweepShared {
     double cta_total;               // CTA sum of a parameter move (CTA-local chains)
     double wsum[4];                 // warp sums of a parameter move's CTA partial
     unsigned long long ep0;         // resident form: epoch base of the neighbour flags
+    unsigned bar_phase;             // top bit of the grid-barrier word before the next barrier
     int abort;
     int last_acc;                   // outcome of the latest parameter decision
     unsigned long long site_acc[2], site_prop[2], nonfinite;
@@ -66,56 +67,80 @@ __device__ __forceinline__ void wait_expired(const Ctx& c)
     atomicExch(&c.st->abort, 1);
 }
 
-// Grid-wide barrier on one 32-bit word: every CTA adds 1, except CTA 0 which
-// adds 2^31 - (G - 1), so the word's top bit flips exactly when all G CTAs
-// have arrived and its low bits return to their old value.  Each CTA waits for
-// the flip relative to the value its own add returned (a fence before the add
-// publishes the CTA's writes; a fence after the wait orders its later reads).
-// The wait is bounded by c.wait_ns: on expiry the CTA flags kStatusTimeout and
-// the abort word, and every CTA leaves the launch at its next wait.
-__device__ __forceinline__ unsigned grid_arrive(const Ctx& c)
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
 {
-    const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
-    __threadfence();
-    if ((int)blockIdx.x != c.skip_cta) return atomicAdd(&c.bar[0], add);
-    return *(volatile unsigned*)&c.bar[0];
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__device__ __forceinline__ bool grid_wait(const Ctx& c, unsigned old)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier on one 32-bit word: every CTA adds 1, except CTA 0 which
+// adds 2^31 - (G - 1), so the word's top bit flips exactly when all G CTAs
+// have arrived and its low bits return to their old value.  Arrival is a
+// release (fence, then a relaxed add that returns nothing); each CTA knows the
+// top bit before the barrier (`phase`, read at launch start and toggled at
+// every barrier) and polls with acquire loads until it flips.  The wait is
+// bounded by c.wait_ns: on expiry the CTA flags kStatusTimeout and the abort
+// word, and every CTA leaves the launch at its next wait.
+__device__ __forceinline__ void grid_arrive(const Ctx& c)
+{
+    const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if ((int)blockIdx.x != c.skip_cta)
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(c.bar), "r"(add) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(const Ctx& c, unsigned phase)
 {
     bool ok = true;
     unsigned spins = 0;
     const unsigned long long t0 = global_ns();
-    while (((old ^ *(volatile unsigned*)&c.bar[0]) & 0x80000000u) == 0u) {
+    while ((ld_acquire_u32(c.bar) >> 31) == phase) {
         if ((++spins & 63u) == 0u) {
             if (*(volatile int*)&c.st->abort) { ok = false; break; }
             if ((long long)(global_ns() - t0) > c.wait_ns) { wait_expired(c); ok = false; break; }
             if (spins > 4096u) __nanosleep(64);
         }
     }
-    __threadfence();
+    return ok;
+}
+
+// One thread: arrive, wait, and toggle the tracked top bit.
+__device__ __forceinline__ bool grid_sync_one(const Ctx& c, unsigned* phase)
+{
+    grid_arrive(c);
+    const bool ok = grid_wait(c, *phase);
+    *phase ^= 1u;
     return ok;
 }
 
 // Whole-CTA form.  Returns false when leaving.
-__device__ bool grid_barrier(const Ctx& c, int* s_abort)
+__device__ bool grid_barrier(const Ctx& c, int* s_abort, unsigned* phase)
 {
     __syncthreads();
-    if (threadIdx.x == 0) *s_abort = !grid_wait(c, grid_arrive(c));
+    if (threadIdx.x == 0) *s_abort = !grid_sync_one(c, phase);
     __syncthreads();
     return !*s_abort;
 }
 
 // Epoch flags between neighbouring CTAs (resident form).  After its sites of
 // parity ph have moved in the sweep with epoch e, a CTA stores e into
-// flags[ph][b] (a fence first publishes its writes); a neighbour waits,
-// bounded, until the flag reaches e.  Epochs only grow over a handle's
-// launches (the host passes the base in c.ep0).
+// flags[ph][b] with a release store (after a CTA barrier, so it publishes the
+// CTA's writes); a neighbour polls, bounded, with acquire loads until the flag
+// reaches e.  Epochs only grow over a handle's launches (the host passes the
+// base in c.ep0).
 __device__ __forceinline__ void flag_post(const Ctx& c, int ph, unsigned long long e)
 {
     if ((int)blockIdx.x == c.skip_cta) return;
-    __threadfence();
-    *(volatile unsigned long long*)&c.flags[ph * kMaxGrid + blockIdx.x] = e;
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(c.flags + ph * kMaxGrid + blockIdx.x), "l"(e)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool flag_wait(const Ctx& c, int ph, int b, unsigned long long e)
@@ -123,15 +148,14 @@ __device__ __forceinline__ bool flag_wait(const Ctx& c, int ph, int b, unsigned 
     bool ok = true;
     unsigned spins = 0;
     const unsigned long long t0 = global_ns();
-    const volatile unsigned long long* f = &c.flags[ph * kMaxGrid + b];
-    while (*f < e) {
+    const unsigned long long* f = c.flags + ph * kMaxGrid + b;
+    while (ld_acquire_u64(f) < e) {
         if ((++spins & 63u) == 0u) {
             if (*(volatile int*)&c.st->abort) { ok = false; break; }
             if ((long long)(global_ns() - t0) > c.wait_ns) { wait_expired(c); ok = false; break; }
             if (spins > 4096u) __nanosleep(64);
         }
     }
-    __threadfence();
     return ok;
 }
 
@@ -386,8 +410,11 @@ __device__ __forceinline__ double cta_partial(const R* tpart, double* wsum)
 // bits.
 struct GridSync {
     static constexpr bool tiled = true;
-    __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort) const { return grid_barrier(c, s_abort); }
-    __device__ __forceinline__ bool arrive_wait(const Ctx& c) const { return grid_wait(c, grid_arrive(c)); }
+    __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort, unsigned* phase) const
+    {
+        return grid_barrier(c, s_abort, phase);
+    }
+    __device__ __forceinline__ bool arrive_wait(const Ctx& c, unsigned* phase) const { return grid_sync_one(c, phase); }
     __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, double v, double*) const
     {
         c.partials[slot * kMaxGrid + blockIdx.x] = v;
@@ -421,12 +448,12 @@ struct GridSync {
 
 struct BlockSync {
     static constexpr bool tiled = false;
-    __device__ __forceinline__ bool barrier(const Ctx&, int*) const
+    __device__ __forceinline__ bool barrier(const Ctx&, int*, unsigned*) const
     {
         __syncthreads();
         return true;
     }
-    __device__ __forceinline__ bool arrive_wait(const Ctx&) const { return true; }
+    __device__ __forceinline__ bool arrive_wait(const Ctx&, unsigned*) const { return true; }
     __device__ __forceinline__ void publish(const Ctx&, unsigned, double v, double* total) const { *total = v; }
     __device__ __forceinline__ double gather(const Ctx&, unsigned, int, const double* total) const
     {
@@ -449,6 +476,7 @@ __device__ __forceinline__ void load_chain_state(const Ctx& c, SweepShared<R, NT
     sh.free_mask = g->free_mask; sh.nred = 0; sh.abort = 0; sh.tr_n = g->tr_n; sh.last_acc = 0;
     sh.site_acc[0] = sh.site_acc[1] = sh.site_prop[0] = sh.site_prop[1] = sh.nonfinite = 0ull;
     sh.ep0 = c.ep0;
+    sh.bar_phase = c.bar ? (*(volatile const unsigned*)c.bar) >> 31 : 0u;
     Model::prep(sh.p, sh.q_cur);
 }
 
@@ -596,7 +624,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
                 my_acc[parity] += site_move<Model, R>(c, kc, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
                 my_prop[parity] += 1ull;
             }
-            if (!sync.barrier(c, &sh.abort)) goto done;
+            if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
         }
 
         // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
@@ -639,7 +667,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
                 const double v = cta_partial<R, NT>(sh.tpart, sh.wsum);
                 if (tid == 0) sync.publish(c, slot, v, &sh.cta_total);
             }
-            if (!sync.barrier(c, &sh.abort)) goto done;
+            if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
             if (tid < 32) {
                 const double v = sync.gather(c, slot, tid, &sh.cta_total);
                 if (tid == 0) decide<R, NT>(sh, l, v);
@@ -657,7 +685,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
             if (record) {
                 record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
-                if (!sync.barrier(c, &sh.abort)) goto done;
+                if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
             }
 
             // ---- step-size adaptation during burn-in (Sec. 4.2) ----
@@ -901,7 +929,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                         // warp 0: publish, grid barrier, gather, decide
                         if (lane == 0) {
                             sync.publish(c, slot, v, &sh.cta_total);
-                            if (!sync.arrive_wait(c)) sh.abort = 1;
+                            if (!sync.arrive_wait(c, &sh.bar_phase)) sh.abort = 1;
                         }
                         __syncwarp();
                         if (!sh.abort) {
@@ -980,7 +1008,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
             const bool record = (s >= c.n_init) && ((s - c.n_init) % c.n_skip == 0);
             if (record) {
                 record_sample<Model, R>(c, n0, n1, sync.lead(), sh.p, sh.J == 0, tid, NT, (const R*)c.F[sh.fidx]);
-                if (!sync.barrier(c, &sh.abort)) goto done;
+                if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
             }
 
             // ---- step-size adaptation during burn-in (Sec. 4.2) ----
