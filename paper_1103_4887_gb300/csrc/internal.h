@@ -13,6 +13,7 @@ constexpr int kMaxParams = 8;
 constexpr int kMaxGrid = 4096;       // upper bound on CTAs of a launch (partials capacity)
 constexpr int kMaxSel = 64;          // histogram components
 constexpr int kMaxBins = 4096;
+constexpr int kDrawChunk = 4096;   // sweeps a launch (the parameter-draw buffer's capacity)
 
 // Scalar sampler state living in device memory.  The sweep kernel keeps a
 // per-CTA copy in shared memory; every CTA evolves it identically (same draws,
@@ -50,6 +51,7 @@ struct Ctx {
     uint64_t ep0;                 // epoch of the sweep before this launch's first (flags only grow)
     unsigned* ticket;             // last-block counter of single-pass reductions
     double* red;                  // [kMaxGrid * 8] per-CTA partials of single-pass reductions
+    const double* pdraw;          // [kDrawChunk][NP][2] parameter draws of a resident launch (z, -log u)
     double *S1, *S2, *shift;      // [D*(M+1) + NP] running shifted sums (FP64)
     double *R1, *R2;              // [(D+1)*M] residual sums: eps_{n+1,a} at a*M+n, delta_n at D*M+n-1
     unsigned long long* hist;     // [n_sel][n_bins + 2]

@@ -41,6 +41,7 @@ struct pimc_handle_s {
     int form = PIMC_FORM_AUTO;            // forms the sweep may take
     unsigned* ticket = nullptr;
     double* red = nullptr;
+    double* pdraw = nullptr;          // parameter draws of a resident launch
     double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
     double *R1 = nullptr, *R2 = nullptr;
     unsigned long long* hist = nullptr;
@@ -109,7 +110,7 @@ Ctx make_ctx(pimc_t h)
     for (int a = 0; a < 4; ++a) c.Rf[a] = h->Rf[a];
     c.X = h->X; c.F[0] = h->F[0]; c.F[1] = h->F[1]; c.y = h->y; c.I = h->I; c.sig = h->sig;
     c.acc_win = h->acc_win; c.st = h->st; c.partials = h->partials; c.bar = h->bar; c.flags = h->flags;
-    c.ticket = h->ticket; c.red = h->red;
+    c.ticket = h->ticket; c.red = h->red; c.pdraw = h->pdraw;
     c.S1 = h->S1; c.S2 = h->S2; c.shift = h->shift;
     c.R1 = h->R1; c.R2 = h->R2;
     c.hist = h->hist; c.h_comp = h->h_comp; c.h_lo = h->h_lo; c.h_hi = h->h_hi;
@@ -228,7 +229,7 @@ int check_finite(const double* v, int64_t n)
 void free_all(pimc_t h)
 {
     void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar, h->flags,
-                    h->ticket, h->red, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
+                    h->ticket, h->red, h->pdraw, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
                     h->dense, h->small, h->y64, h->I64, h->trace, h->R1, h->R2, h->hmc.hs, h->hmc.Q, h->hmc.P,
                     h->hmc.g, h->hmc.invm};
     for (void* b : bufs)
@@ -306,6 +307,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         {(void**)&h->flags, sizeof(unsigned long long) * 2 * kMaxGrid},
         {(void**)&h->ticket, sizeof(unsigned) * 4},
         {(void**)&h->red, sizeof(double) * 8 * kMaxGrid},
+        {(void**)&h->pdraw, sizeof(double) * 2 * kMaxParams * kDrawChunk},
         {(void**)&h->S1, sizeof(double) * nc},
         {(void**)&h->S2, sizeof(double) * nc},
         {(void**)&h->shift, sizeof(double) * nc},
@@ -538,7 +540,7 @@ int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed)
     if (n_sweeps < 0) return fail(h, PIMC_ERR_ARG, "n_sweeps < 0");
     Ctx c = make_ctx(h);
     c.seed = seed;
-    const int64_t chunk = 4096;  // bound the duration of one launch
+    const int64_t chunk = kDrawChunk;  // bound the duration of one launch
     for (int64_t done = 0; done < n_sweeps; done += chunk) {
         const int64_t k = std::min<int64_t>(chunk, n_sweeps - done);
         c.ep0 = h->epoch;

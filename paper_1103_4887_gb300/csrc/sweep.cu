@@ -246,18 +246,16 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
     u = Num<R>::uni(w.x, w.y);
 }
 
-// One site move from operands in registers: proposal x' = x + sigma z, its
-// cached value, Delta A_n, and the Metropolis decision written as
-// dA < -log u (Eq. (Paccept); NaN compares false).
+// A site move from operands in registers, in two halves.  The proposal:
+// x' = x + sigma z, its cached value, and -log u of the accept uniform.
 template <class Model, class R>
-__device__ __forceinline__ bool site_core(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
-                                          R beta, const R* x, const R* sg, R drive, const Nbhd<R, Model::D>& nb,
-                                          R* xp, R* gp, unsigned long long& nonfinite)
+__device__ __forceinline__ void site_propose(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
+                                             const R* x, const R* sg, R drive, R* xp, R* gp, R& E)
 {
     constexpr int D = Model::D;
     R z[D], u;
     site_draws<Model, R>(c, s, n, z, u);
-    const R E = neglog<R>(u);
+    E = neglog<R>(u);
 #pragma unroll
     for (int a = 0; a < D; ++a) xp[a] = x[a] + sg[a] * z[a];
     if (n < cache_len(c)) cache_value_at<Model, R>(c, k, xp, pr, drive, gp);
@@ -265,9 +263,28 @@ __device__ __forceinline__ bool site_core(const Ctx& c, const Coef<R>& k, int64_
 #pragma unroll
         for (int a = 0; a < D; ++a) gp[a] = R(0);
     }
+}
+
+// The decision: Delta A_n and the Metropolis rule written as dA < -log u
+// (Eq. (Paccept); NaN compares false).
+template <class Model, class R>
+__device__ __forceinline__ bool site_decide(const Ctx& c, const Coef<R>& k, int64_t n, const R* x, const R* xp,
+                                            const R* gp, R beta, R E, const Nbhd<R, Model::D>& nb,
+                                            unsigned long long& nonfinite)
+{
     const R dA = site_delta<Model, R>(c, k, n, x, xp, gp, beta, nb);
     if (!isfinite(dA)) ++nonfinite;
     return dA < E;
+}
+
+template <class Model, class R>
+__device__ __forceinline__ bool site_core(const Ctx& c, const Coef<R>& k, int64_t n, long long s, const R* pr,
+                                          R beta, const R* x, const R* sg, R drive, const Nbhd<R, Model::D>& nb,
+                                          R* xp, R* gp, unsigned long long& nonfinite)
+{
+    R E;
+    site_propose<Model, R>(c, k, n, s, pr, x, sg, drive, xp, gp, E);
+    return site_decide<Model, R>(c, k, n, x, xp, gp, beta, E, nb, nonfinite);
 }
 
 // General form of a site move: operands from global memory, store on accept.
@@ -480,27 +497,43 @@ __device__ __forceinline__ void load_chain_state(const Ctx& c, SweepShared<R, NT
     Model::prep(sh.p, sh.q_cur);
 }
 
-// This sweep's proposal for parameter l (one thread per parameter).  p_l
-// changes only in its own move, so p'_l = p_l + sigma_l z_l is fixed at the
-// sweep's start; the proposed vector of move l is completed after the earlier
-// moves from q_new[l] (components l, and 7 with l = 6).
-template <class Model, class R, int NT>
-__device__ __forceinline__ void draw_param_proposal(const Ctx& c, SweepShared<R, NT>& sh, long long s, int l)
+// The parameter-move draws of sweep s, parameter l (Philox kind 1): the
+// proposal increment z (Box-Muller normal, or U(-1, 1)) and -log u of the
+// accept uniform.
+__device__ __forceinline__ void param_draw(const Ctx& c, long long s, int l, double& z, double& elog)
 {
-    if (!((sh.free_mask >> l) & 1u)) return;
-    double z0, z1;
+    double z1;
     const uint4 wz = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u);
-    if (c.proposal == kProposalUniform) z0 = 2.0 * u01d(wz.x, wz.y) - 1.0;
-    else Num<double>::box_muller(wz, z0, z1);
+    if (c.proposal == kProposalUniform) z = 2.0 * u01d(wz.x, wz.y) - 1.0;
+    else Num<double>::box_muller(wz, z, z1);
     const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
-    const double pl = sh.p[l] + sh.sigp[l] * z0;
+    elog = -log(u01d(w.x, w.y));
+}
+
+// This sweep's proposal for parameter l (one thread per parameter) from its
+// draws.  p_l changes only in its own move, so p'_l = p_l + sigma_l z_l is
+// fixed at the sweep's start; the proposed vector of move l is completed after
+// the earlier moves from q_new[l] (components l, and 7 with l = 6).
+template <class Model, class R, int NT>
+__device__ __forceinline__ void set_param_proposal(SweepShared<R, NT>& sh, int l, double z, double elog)
+{
+    const double pl = sh.p[l] + sh.sigp[l] * z;
     sh.pnew[l] = pl;
-    sh.elog[l] = -log(u01d(w.x, w.y));
+    sh.elog[l] = elog;
     sh.inbox[l] = (pl >= sh.lo[l] && pl <= sh.hi[l]) ? 1 : 0;
     double pv[kMaxP];
 #pragma unroll
     for (int q = 0; q < kMaxP; ++q) pv[q] = (q == l) ? pl : sh.p[q];
     Model::prep(pv, sh.q_new[l]);
+}
+
+template <class Model, class R, int NT>
+__device__ __forceinline__ void draw_param_proposal(const Ctx& c, SweepShared<R, NT>& sh, long long s, int l)
+{
+    if (!((sh.free_mask >> l) & 1u)) return;
+    double z, elog;
+    param_draw(c, s, l, z, elog);
+    set_param_proposal<Model, R, NT>(sh, l, z, elog);
 }
 
 // The model-parameter vector of move l applied to q (components l, and 7
@@ -795,7 +828,12 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
     for (int64_t k = 0; k < n_sweeps; ++k) {
         const long long s = sh.sweep;
         const unsigned long long ep = sh.ep0 + (unsigned long long)k + 1ull;
-        if (tid < NP) draw_param_proposal<Model, R, NT>(c, sh, s, tid);
+        // this sweep's parameter draws, evaluated before the launch by
+        // param_draws_kernel (FP64 transcendental functions issue slowly on one
+        // warp and would hold up the even phase)
+        if (tid < NP && ((sh.free_mask >> tid) & 1u))
+            set_param_proposal<Model, R, NT>(sh, tid, __ldg(c.pdraw + 2 * (k * NP + tid)),
+                                             __ldg(c.pdraw + 2 * (k * NP + tid) + 1));
         const R beta = R(sh.beta);
         R pr[kMaxP];
 #pragma unroll
@@ -805,6 +843,10 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
 #pragma unroll
         for (int parity = 0; parity < 2; ++parity) {
             if (own && (int)(n & 1) == parity) {
+                // the proposal first: it needs no neighbour, so it overlaps the
+                // halo wait of the tile's boundary sites
+                R xp[D], gp[D], E;
+                site_propose<Model, R>(c, kc, n, s, pr, xr, sgr, drive, xp, gp, E);
                 Nbhd<R, D> nb;
                 R xl[D], gl[D];
 #pragma unroll
@@ -848,8 +890,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                         nb.gn1[a] = trap ? ((i + 1 < T) ? sh.gs[a][i + 1] : gh[a]) : R(0);
                     }
                 }
-                R xp[D], gp[D];
-                if (ok && site_core<Model, R>(c, kc, n, s, pr, beta, xr, sgr, drive, nb, xp, gp, my_nf)) {
+                if (ok && site_decide<Model, R>(c, kc, n, xr, xp, gp, beta, E, nb, my_nf)) {
                     R* Fw = (R*)c.F[sh.fidx];
 #pragma unroll
                     for (int a = 0; a < D; ++a) {
@@ -1053,6 +1094,21 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
     sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
 }
 
+// The parameter draws of the next n sweeps of a chain, one thread a (sweep,
+// parameter): out[2 (k NP + l)] = z, out[2 (k NP + l) + 1] = -log u for sweep
+// st->sweep + k.  The same values the sweep draws itself (param_draw).
+template <int NP>
+__global__ void __launch_bounds__(256) param_draws_kernel(Ctx c, int64_t n, double* out)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * NP) return;
+    const int l = (int)(idx % NP);
+    double z = 0.0, elog = 0.0;
+    if ((c.st->free_mask >> l) & 1u) param_draw(c, c.st->sweep + idx / NP, l, z, elog);
+    out[2 * idx] = z;
+    out[2 * idx + 1] = elog;
+}
+
 // Resident form (FP32-mixed): tiles of at most kSweepBlock - 32 sites, even
 // when there are several.  It evaluates two maps per site and parameter move
 // to take them off the critical path, which pays where the sweep is bound by
@@ -1113,8 +1169,14 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
     Ctx cc = c;
     int64_t ns = n_sweeps;
     void* args[] = {(void*)&cc, (void*)&ns};
-    const void* k = (resident && resident_fits(prec_of<R>(), c.tile, grid)) ? SweepKernels<Model, R>::resident()
-                                                                            : SweepKernels<Model, R>::general();
+    const bool res = resident && resident_fits(prec_of<R>(), c.tile, grid) && c.pdraw && n_sweeps <= kDrawChunk;
+    if (res && n_sweeps > 0) {
+        const int64_t nt = n_sweeps * Model::NP;
+        param_draws_kernel<Model::NP><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c, n_sweeps, const_cast<double*>(c.pdraw));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, 0, s);
 }
 
