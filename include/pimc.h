@@ -323,6 +323,13 @@ int pimc_set_wait_limit(pimc_t h, int64_t ns);
 /* Make CTA `cta` skip its barrier arrivals in later sweeps (-1: off), so the
  * other CTAs' bounded waits expire and pimc_sync reports PIMC_ERR_TIMEOUT. */
 int pimc_debug_skip_arrive(pimc_t h, int cta);
+/* The exact sum that parameter moves use for their change of action, applied
+ * to n caller terms (host array, copied): *out = the sum of terms[0..n), each
+ * first rounded to FP32 when as_float != 0, computed on the current device in
+ * 42-bit integer chunks of 2^-64 and rounded once to FP64; terms of magnitude
+ * >= 2^62 count as infinite, NaN gives NaN.  No handle; synchronous.
+ * PIMC_ERR_ARG for n < 0 or n > 2^20, PIMC_ERR_CUDA on a device error. */
+int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out);
 /* Force the sweep grid size (0: automatic). */
 int pimc_set_grid(pimc_t h, int grid);
 

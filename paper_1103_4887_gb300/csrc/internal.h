@@ -45,7 +45,7 @@ struct Ctx {
     void* sig;                    // R[D][ldx]
     uint32_t* acc_win;            // [ldx] accepted moves per site in the adaptation window
     DevState* st;
-    double* partials;             // [2][kMaxGrid] per-CTA parameter-move sums
+    double* partials;             // [3][4] u64 accumulator slots of the exact parameter-move sums
     unsigned* bar;                // [0] the grid barrier's word
     unsigned long long* flags;    // [2][kMaxGrid] neighbour epoch flags of the sweep
     uint64_t ep0;                 // epoch of the sweep before this launch's first (flags only grow)
@@ -115,6 +115,8 @@ cudaError_t launch_site_delta(int model, int prec, const Ctx& c, const double* X
                               double* dA, cudaStream_t s);
 cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double pl_new, double beta,
                                double* out, cudaStream_t s);
+// Exact Fix3 sum of n device terms (as FP32 when as_float) into *out (device).
+cudaError_t launch_fix_sum(const double* t, int64_t n, int as_float, double* out, cudaStream_t s);
 // dst[i] = (storage type) src[i], i < n.
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s);
 // Ensemble forecast from the current state: out[e][a][k] (device, FP64).

@@ -946,6 +946,25 @@ int pimc_set_wait_limit(pimc_t h, int64_t ns)
     return PIMC_OK;
 }
 
+int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out)
+{
+    if (n < 0 || n > (1 << 20) || (n > 0 && !terms) || !out) {
+        set_thread_error("pimc_debug_fix_sum: 0 <= n <= 2^20 terms and an output are required");
+        return PIMC_ERR_ARG;
+    }
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * (size_t)(n + 1));
+    if (e == cudaSuccess && n > 0) e = cudaMemcpy(d, terms, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_fix_sum(d, n, as_float, d + n, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + n, sizeof(double), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        set_thread_error(cudaGetErrorString(e));
+        return PIMC_ERR_CUDA;
+    }
+    return PIMC_OK;
+}
+
 int pimc_debug_skip_arrive(pimc_t h, int cta)
 {
     if (!h) return PIMC_ERR_ARG;

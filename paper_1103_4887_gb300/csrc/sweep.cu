@@ -29,6 +29,14 @@
 
 namespace pimc {
 
+// An exact sum of parameter-move terms (see "exact sums" below).
+struct Fix3 {
+    long long c[3];
+    unsigned long long flags;
+};
+
+constexpr long long kFixMask = (1ll << 42) - 1;
+
 template <class R, int NT> struct SweepShared {
     double p[kMaxP], lo[kMaxP], hi[kMaxP], sigp[kMaxP];
     double beta;
@@ -40,12 +48,11 @@ template <class R, int NT> struct SweepShared {
     int inbox[kMaxP];
     R q_cur[kMaxP];                   // current model parameters in R
     R q_new[kMaxP][kMaxP];            // proposed vector for each parameter move, in R
-    R tpart[NT];                    // per-thread partial sums of a parameter move
     R halo[kMaxD];                  // trapezoid: F(x_{n1}, p') of the next tile's first site
     R xs[kMaxD][NT];                // resident form: x of site n0 + i at [a][i]
     R gs[kMaxD][NT];                // resident form: cached value of site n0 + i at [a][i]
-    double cta_total;               // CTA sum of a parameter move (CTA-local chains)
-    double wsum[4];                 // warp sums of a parameter move's CTA partial
+    Fix3 wfix[NT / 32];             // warp sums of a parameter move's exact CTA sum
+    Fix3 cta_fix;                   // CTA sum of a parameter move (CTA-local chains)
     unsigned long long ep0;         // resident form: epoch base of the neighbour flags
     unsigned bar_phase;             // top bit of the grid-barrier word before the next barrier
     int abort;
@@ -400,31 +407,125 @@ __device__ __forceinline__ double block_sum(double v, double* wsum)
     return t;
 }
 
-// FP64 sum of the NT per-thread partials of a parameter move, from the
-// per-thread values up, by warps 0..3 (spread over the SM's four schedulers,
-// whose FP64 issue is slow): warp q adds entries [q NT/4, (q+1) NT/4) per lane
-// in index order, then across lanes; the four warp sums meet in shared memory
-// after a named barrier of threads 0..127.  Called by threads 0..127 (a CTA
-// barrier after the partials were written); valid in all of them.
-template <class R, int NT>
-__device__ __forceinline__ double cta_partial(const R* tpart, double* wsum)
+// ---- exact sums of parameter-move terms ---------------------------------------
+// A term t enters as the integer T = t 2^64 truncated toward zero (|t| < 2^62;
+// terms below 2^-64 vanish), held in three signed 64-bit chunks of 42 bits,
+// T = c0 + c1 2^42 + c2 2^84.  Chunk-wise integer additions of up to 2^21
+// terms neither overflow nor round, so the change of action of a parameter
+// move is summed exactly and in no particular order: every CTA, tiling and
+// form obtains the same bits, and the result, rounded once to FP64, is at
+// least as accurate as an FP64 summation.  Infinite terms (|t| >= 2^62) and
+// NaN set flags (1: +inf, 2: -inf, 4: NaN) that make the total +-inf or NaN.
+// (struct Fix3: see "exact sums of parameter-move terms" below)
+
+__device__ __forceinline__ void fix_zero(Fix3& f)
 {
-    const int tid = threadIdx.x, lane = tid & 31, q = tid >> 5;
-    constexpr int kPer = NT / 128;
-    double v = (double)tpart[q * (NT / 4) + lane];
+    f.c[0] = f.c[1] = f.c[2] = 0;
+    f.flags = 0ull;
+}
+
+// Adds sign * m 2^e2 for an integer m < 2^53.
+__device__ __forceinline__ void fix_add_parts(Fix3& f, unsigned long long m, int e2, bool neg)
+{
+    const int sh = e2 + 64;  // bit of T that m's bit 0 lands on
+    if (m != 0ull && sh + (64 - __clzll((long long)m)) > 126) {
+        f.flags |= neg ? 2ull : 1ull;
+        return;
+    }
 #pragma unroll
-    for (int k = 1; k < kPer; ++k) v += (double)tpart[q * (NT / 4) + lane + 32 * k];
-    v = warp_sum(v);
-    if (lane == 0) wsum[q] = v;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    return (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
+    for (int j = 0; j < 3; ++j) {
+        const int d = sh - 42 * j;
+        unsigned long long v = 0ull;
+        if (d >= 0) v = (d < 42) ? ((m << d) & (unsigned long long)kFixMask) : 0ull;
+        else v = (-d < 64) ? ((m >> (-d)) & (unsigned long long)kFixMask) : 0ull;
+        f.c[j] += neg ? -(long long)v : (long long)v;
+    }
+}
+
+__device__ __forceinline__ void fix_add(Fix3& f, float t)
+{
+    const unsigned b = __float_as_uint(t);
+    const unsigned ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+    const bool neg = (b >> 31) != 0u;
+    if (ex == 0xffu) f.flags |= man ? 4ull : (neg ? 2ull : 1ull);
+    else if (ex == 0u) fix_add_parts(f, man, -149, neg);
+    else fix_add_parts(f, man | 0x800000u, (int)ex - 150, neg);
+}
+
+__device__ __forceinline__ void fix_add(Fix3& f, double t)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    const int ex = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long man = b & ((1ull << 52) - 1ull);
+    const bool neg = (b >> 63) != 0ull;
+    if (ex == 0x7ff) f.flags |= man ? 4ull : (neg ? 2ull : 1ull);
+    else if (ex == 0) fix_add_parts(f, man, -1074, neg);
+    else fix_add_parts(f, man | (1ull << 52), ex - 1075, neg);
+}
+
+__device__ __forceinline__ void fix_normalize(Fix3& f)
+{
+    f.c[1] += f.c[0] >> 42;
+    f.c[0] &= kFixMask;
+    f.c[2] += f.c[1] >> 42;
+    f.c[1] &= kFixMask;
+}
+
+// The sum as a double: carries normalised (c0, c1 in [0, 2^42), the sign in
+// c2), the magnitude formed from non-negative chunks added from the low one up
+// (two roundings at most, no cancellation), then the sign.
+__device__ __forceinline__ double fix_value(Fix3 f)
+{
+    if (f.flags) {
+        if ((f.flags & 4ull) || (f.flags & 3ull) == 3ull) return __longlong_as_double(0x7ff8000000000000ll);
+        return __longlong_as_double((f.flags & 1ull) ? 0x7ff0000000000000ll : (long long)0xfff0000000000000ull);
+    }
+    fix_normalize(f);
+    const bool neg = f.c[2] < 0;
+    if (neg) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f.c[j] = -f.c[j];
+        fix_normalize(f);
+    }
+    const double mag = fma((double)f.c[2], 0x1p20, fma((double)f.c[1], 0x1p-22, (double)f.c[0] * 0x1p-64));
+    return neg ? -mag : mag;
+}
+
+// CTA sum of every thread's Fix3 (one CTA barrier inside), carries
+// normalised; valid in thread 0.
+template <int NT>
+__device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f.c[j] += __shfl_xor_sync(0xffffffffu, f.c[j], off);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) f.flags |= __shfl_xor_sync(0xffffffffu, f.flags, off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wfix[w] = f;
+    __syncthreads();
+    Fix3 t;
+    fix_zero(t);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NT / 32; ++k) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t.c[j] += wfix[k].c[j];
+            t.flags |= wfix[k].flags;
+        }
+        fix_normalize(t);
+    }
+    return t;
 }
 
 // Synchronisation policies of a chain's sweep.  GridSync: the chain is tiled
-// over all CTAs of a cooperative launch (grid barriers, every CTA sums all CTA
-// partials in the same order).  BlockSync: one CTA owns the whole chain
-// (CTA barriers, the CTA sum is the total).  With one CTA both give the same
-// bits.
+// over all CTAs of a cooperative launch (grid barriers; each CTA adds its exact
+// partial into a slot of three integer accumulators before the barrier of a
+// parameter move and reads the total after it).  BlockSync: one CTA owns the
+// whole chain (CTA barriers, the CTA sum is the total).  Both give the same
+// bits for the same chain.  Slots rotate over three (a slot is cleared by CTA
+// 0 one move after its use, when every CTA has read it; the host clears all
+// before each launch).
 struct GridSync {
     static constexpr bool tiled = true;
     __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort, unsigned* phase) const
@@ -432,33 +533,33 @@ struct GridSync {
         return grid_barrier(c, s_abort, phase);
     }
     __device__ __forceinline__ bool arrive_wait(const Ctx& c, unsigned* phase) const { return grid_sync_one(c, phase); }
-    __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, double v, double*) const
+    // thread 0, before the barrier
+    __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, const Fix3& f, Fix3*) const
     {
-        c.partials[slot * kMaxGrid + blockIdx.x] = v;
+        unsigned long long* acc = (unsigned long long*)c.partials + 4 * slot;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(acc + j), "l"((unsigned long long)f.c[j])
+                         : "memory");
+        if (f.flags) asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(acc + 3), "l"(f.flags) : "memory");
     }
-    // Warp-wide: every lane loads its CTAs' partials (independent loads, one
-    // L2 round trip), adds them in index order (only the groups that exist:
-    // each FP64 add costs many issue cycles), then across lanes; valid in
-    // every lane.
-    __device__ __forceinline__ double gather(const Ctx& c, unsigned slot, int lane, const double*) const
+    // thread 0, after the barrier
+    __device__ __forceinline__ double total(const Ctx& c, unsigned slot, const Fix3*) const
     {
-        const int G = (int)gridDim.x;
-        const double* part = c.partials + slot * kMaxGrid;
-        double v = 0.0;
-        for (int base = 0; base < G; base += 256) {
-            double t[8];
+        const unsigned long long* acc = (const unsigned long long*)c.partials + 4 * slot;
+        Fix3 t;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int i = base + lane + 32 * j;
-                t[j] = (i < G) ? __ldcg(part + i) : 0.0;
-            }
+        for (int j = 0; j < 3; ++j) t.c[j] = (long long)__ldcg(acc + j);
+        t.flags = __ldcg(acc + 3);
+        return fix_value(t);
+    }
+    // thread 0, after reading the total of `slot`: clear the previous slot
+    __device__ __forceinline__ void recycle(const Ctx& c, unsigned slot) const
+    {
+        if (blockIdx.x != 0) return;
+        unsigned long long* acc = (unsigned long long*)c.partials + 4 * ((slot + 2u) % 3u);
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (base + 32 * j < G) v += t[j];
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        return v;
+        for (int j = 0; j < 4; ++j) __stcg(acc + j, 0ull);
     }
     __device__ __forceinline__ bool lead() const { return blockIdx.x == 0; }
 };
@@ -471,11 +572,9 @@ struct BlockSync {
         return true;
     }
     __device__ __forceinline__ bool arrive_wait(const Ctx&, unsigned*) const { return true; }
-    __device__ __forceinline__ void publish(const Ctx&, unsigned, double v, double* total) const { *total = v; }
-    __device__ __forceinline__ double gather(const Ctx&, unsigned, int, const double* total) const
-    {
-        return *(volatile const double*)total;
-    }
+    __device__ __forceinline__ void publish(const Ctx&, unsigned, const Fix3& f, Fix3* cta) const { *cta = f; }
+    __device__ __forceinline__ double total(const Ctx&, unsigned, const Fix3* cta) const { return fix_value(*cta); }
+    __device__ __forceinline__ void recycle(const Ctx&, unsigned) const {}
     __device__ __forceinline__ bool lead() const { return true; }
 };
 
@@ -671,10 +770,11 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             apply_move<R, NT>(pq, sh, l);
             const R* Fc = (const R*)c.F[sh.fidx];
             R* Fn = (R*)c.F[sh.fidx ^ 1u];
-            R part = R(0);
+            Fix3 part;
+            fix_zero(part);
             const int64_t nend = min(n1, M);
             if (c.scheme == kSchemeRK4) {
-                for (int64_t n = n0 + tid; n < nend; n += NT) part += param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn);
+                for (int64_t n = n0 + tid; n < nend; n += NT) fix_add(part, param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn));
             } else {
                 // trapezoid: F(x_n, p') of the tile (and of the next tile's
                 // first site, recomputed here), then the residual changes
@@ -690,20 +790,17 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
                     R gn1p[D];
 #pragma unroll
                     for (int a = 0; a < D; ++a) gn1p[a] = (n + 1 < n1) ? Fn[a * c.ldf + n + 1] : sh.halo[a];
-                    part += trap_term<Model, R>(c, kc, n, beta, Fc, Fn, gn1p);
+                    fix_add(part, trap_term<Model, R>(c, kc, n, beta, Fc, Fn, gn1p));
                 }
             }
-            sh.tpart[tid] = part;
-            __syncthreads();
-            const unsigned slot = sh.nred & 1u;
-            if (tid < 128) {
-                const double v = cta_partial<R, NT>(sh.tpart, sh.wsum);
-                if (tid == 0) sync.publish(c, slot, v, &sh.cta_total);
-            }
+            // exact sum: CTA, then grid (accumulator slot), then the decision
+            const unsigned slot = sh.nred % 3u;
+            const Fix3 cta = fix_cta_sum<NT>(part, sh.wfix);
+            if (tid == 0) sync.publish(c, slot, cta, &sh.cta_fix);
             if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
-            if (tid < 32) {
-                const double v = sync.gather(c, slot, tid, &sh.cta_total);
-                if (tid == 0) decide<R, NT>(sh, l, v);
+            if (tid == 0) {
+                decide<R, NT>(sh, l, sync.total(c, slot, &sh.cta_fix));
+                sync.recycle(c, slot);
             }
             __syncthreads();
 #pragma unroll
@@ -793,9 +890,6 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
     const bool left_halo = own && i == 0 && n0 >= 1;
     const bool right_halo = own && i == T - 1 && n1 <= M;
     const int b = (int)blockIdx.x;
-    // partial of site n0 + i at tpart[i], zeros above the tile (warp 0 fills
-    // the top 32): the CTA sum then adds in the general form's order
-    const int tslot = (tid >= 32) ? i : NT - 32 + tid;
     R* X = (R*)c.X;
     R* sig = (R*)c.sig;
 
@@ -943,39 +1037,36 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                 }
                 // first move: no decision pending
                 int l = __ffs(todo) - 1;
-                R part = R(0);
+                Fix3 mine;
+                fix_zero(mine);
                 if (own) {
                     R q[kMaxP];
 #pragma unroll
                     for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
                     apply_move<R, NT>(q, sh, l);
                     move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f, fn);
-                    if (has_next) part = move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta);
+                    if (has_next) fix_add(mine, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta));
                     if (cached) {
                         R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
                         for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
                     }
                 }
-                sh.tpart[tslot] = part;
-                __syncthreads();
                 while (true) {
                     todo &= todo - 1u;
                     const int l2 = todo ? __ffs(todo) - 1 : -1;
                     R fA[D], fnA[D], fR[D], fnR[D];
-                    const unsigned slot = sh.nred & 1u;
-                    double v = 0.0;
-                    if (tid < 128) v = cta_partial<R, NT>(sh.tpart, sh.wsum);
+                    const unsigned slot = sh.nred % 3u;
+                    const Fix3 cta = fix_cta_sum<NT>(mine, sh.wfix);  // exact CTA sum (a CTA barrier inside)
                     if (tid < 32) {
-                        // warp 0: publish, grid barrier, gather, decide
+                        // thread 0: publish, grid barrier, total, decide
                         if (lane == 0) {
-                            sync.publish(c, slot, v, &sh.cta_total);
+                            sync.publish(c, slot, cta, &sh.cta_fix);
                             if (!sync.arrive_wait(c, &sh.bar_phase)) sh.abort = 1;
-                        }
-                        __syncwarp();
-                        if (!sh.abort) {
-                            const double tot = sync.gather(c, slot, lane, &sh.cta_total);
-                            if (lane == 0) decide<R, NT>(sh, l, tot);
+                            else {
+                                decide<R, NT>(sh, l, sync.total(c, slot, &sh.cta_fix));
+                                sync.recycle(c, slot);
+                            }
                         }
                     } else if (own && l2 >= 0) {
                         // speculation: move l2's values for both outcomes of
@@ -1017,22 +1108,20 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     }
                     if (l2 < 0) break;
                     l = l2;
-                    part = R(0);
+                    fix_zero(mine);
                     if (own) {
 #pragma unroll
                         for (int a = 0; a < D; ++a) {
                             f[a] = acc ? fA[a] : fR[a];
                             fn[a] = acc ? fnA[a] : fnR[a];
                         }
-                        if (has_next) part = move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta);
+                        if (has_next) fix_add(mine, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta));
                         if (cached) {
                             R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
                             for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
                         }
                     }
-                    sh.tpart[tslot] = part;
-                    __syncthreads();
                 }
                 if (own) {
 #pragma unroll
@@ -1176,6 +1265,9 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    // the three accumulator slots of the exact parameter-move sums start at zero
+    const cudaError_t e = cudaMemsetAsync(c.partials, 0, 12 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, 0, s);
 }
@@ -1282,47 +1374,73 @@ __global__ void __launch_bounds__(kBlock) site_delta_kernel(Ctx c, const double*
     dA[n] = (double)site_delta<Model, R>(c, kc, n, x, xp, fp, R(beta), nb);
 }
 
-// Full-path parameter change of action: per-CTA sums in FP64, then the last
-// CTA to finish adds them in CTA order (single pass, deterministic).  For the
-// trapezoid rule the new field of every site is written first
-// (trap_field_kernel) and read by this kernel.
+// Full-path parameter change of action, summed exactly like the sweep's
+// parameter moves (Fix3): per-CTA sums added into an accumulator slot, then
+// the last CTA to finish (ticket) rounds the total once.  For the trapezoid
+// rule the new field of every site is written first (trap_field_kernel) and
+// read by this kernel.
 template <class Model, class R>
 __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, double pl_new, double beta, double* out)
 {
-    __shared__ double wsum[kBlock / 32];
+    __shared__ Fix3 wfix[kBlock / 32];
     __shared__ int last;
     const R* Fc = (const R*)c.F[c.st->fidx];
     R* Fn = (R*)c.F[c.st->fidx ^ 1u];
     double pd[kMaxP];
-    for (int q = 0; q < kMaxP; ++q) pd[q] = c.st->p[q];
-    pd[l] = pl_new;
+#pragma unroll
+    for (int q = 0; q < kMaxP; ++q) pd[q] = (q == l) ? pl_new : c.st->p[q];
     R pq[kMaxP];
     Model::prep(pd, pq);
     const Coef<R> kc(c);
-    R part = R(0);
+    Fix3 part;
+    fix_zero(part);
     for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < c.M; n += (int64_t)gridDim.x * kBlock) {
         if (c.scheme == kSchemeRK4) {
-            part += param_term<Model, R>(c, kc, n, pq, R(beta), Fc, Fn);
+            fix_add(part, param_term<Model, R>(c, kc, n, pq, R(beta), Fc, Fn));
         } else {
             R gn1p[Model::D];
             for (int a = 0; a < Model::D; ++a) gn1p[a] = Fn[a * c.ldf + n + 1];
-            part += trap_term<Model, R>(c, kc, n, R(beta), Fc, Fn, gn1p);
+            fix_add(part, trap_term<Model, R>(c, kc, n, R(beta), Fc, Fn, gn1p));
         }
     }
-    const double bs = block_sum<kBlock>((double)part, wsum);
+    const Fix3 cta = fix_cta_sum<kBlock>(part, wfix);
+    unsigned long long* acc = (unsigned long long*)c.red;
     if (threadIdx.x == 0) {
-        c.red[blockIdx.x] = bs;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(acc + j, (unsigned long long)cta.c[j]);
+        if (cta.flags) atomicOr(acc + 3, cta.flags);
         __threadfence();
         last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        double t = 0.0;
-        for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(&c.red[i]);
-        *out = t;
+        Fix3 t;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) t.c[j] = (long long)__ldcg(acc + j);
+        t.flags = __ldcg(acc + 3);
+        *out = fix_value(t);
         *c.ticket = 0u;
     }
+}
+
+// The exact sum of n terms by one CTA (the test hook of the Fix3 arithmetic).
+template <class T>
+__global__ void __launch_bounds__(256) fix_sum_kernel(const double* t, int64_t n, double* out)
+{
+    __shared__ Fix3 wfix[256 / 32];
+    Fix3 f;
+    fix_zero(f);
+    for (int64_t i = threadIdx.x; i < n; i += 256) fix_add(f, (T)t[i]);
+    const Fix3 s = fix_cta_sum<256>(f, wfix);
+    if (threadIdx.x == 0) *out = fix_value(s);
+}
+
+cudaError_t launch_fix_sum(const double* t, int64_t n, int as_float, double* out, cudaStream_t s)
+{
+    if (as_float) fix_sum_kernel<float><<<1, 256, 0, s>>>(t, n, out);
+    else fix_sum_kernel<double><<<1, 256, 0, s>>>(t, n, out);
+    return cudaGetLastError();
 }
 
 template <class Model, class R>
@@ -1358,6 +1476,8 @@ static cudaError_t param_delta_t(const Ctx& c, int l, double pl, double beta, do
     int grid = (int)((c.M + kBlock - 1) / kBlock);
     if (grid > kMaxGrid) grid = kMaxGrid;
     if (grid < 1) grid = 1;
+    const cudaError_t e = cudaMemsetAsync(c.red, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     param_delta_kernel<Model, R><<<grid, kBlock, 0, s>>>(c, l, pl, beta, out);
     return cudaGetLastError();
 }

@@ -35,7 +35,7 @@ EXPORTS = [
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
-    "pimc_debug_skip_arrive", "pimc_set_grid", "pimc_action_static",
+    "pimc_debug_skip_arrive", "pimc_debug_fix_sum", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
     "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
 ]
@@ -116,6 +116,7 @@ def _declare(L):
         "pimc_checkpoint_load": [_vp, ctypes.c_char_p],
         "pimc_set_wait_limit": [_vp, _i64],
         "pimc_debug_skip_arrive": [_vp, _int],
+        "pimc_debug_fix_sum": [_vp, _i64, _int, _vp],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
         "pimc_batch_create": [_vp, _vp, _int],
@@ -152,6 +153,17 @@ def action_static(model, M, dt, Rm, Rf, X_ptr, p_ptr, y_ptr, I_ptr, out_ptr, str
                              _vp(y_ptr), _vp(I_ptr), _vp(out_ptr), _vp(stream_ptr))
     if r != OK:
         raise PimcError(r, L.pimc_last_error(None).decode())
+
+
+def debug_fix_sum(terms, as_float=False):
+    """The exact sum parameter moves use, applied to a host array (test hook)."""
+    L = load()
+    t = _f64(terms)
+    out = np.zeros(1)
+    r = L.pimc_debug_fix_sum(_p(t), int(t.size), 1 if as_float else 0, _p(out))
+    if r != OK:
+        raise PimcError(r, L.pimc_last_error(None).decode())
+    return float(out[0])
 
 
 class Sampler:
