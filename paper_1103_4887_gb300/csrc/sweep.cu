@@ -424,7 +424,8 @@ __device__ __forceinline__ void fix_zero(Fix3& f)
     f.flags = 0ull;
 }
 
-// Adds sign * m 2^e2 for an integer m < 2^53.
+// Adds sign * m 2^e2 for an integer m < 2^53: T = m 2^(e2 + 64) as a 128-bit
+// integer (hi:lo), cut into the three chunks.
 __device__ __forceinline__ void fix_add_parts(Fix3& f, unsigned long long m, int e2, bool neg)
 {
     const int sh = e2 + 64;  // bit of T that m's bit 0 lands on
@@ -432,14 +433,20 @@ __device__ __forceinline__ void fix_add_parts(Fix3& f, unsigned long long m, int
         f.flags |= neg ? 2ull : 1ull;
         return;
     }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int d = sh - 42 * j;
-        unsigned long long v = 0ull;
-        if (d >= 0) v = (d < 42) ? ((m << d) & (unsigned long long)kFixMask) : 0ull;
-        else v = (-d < 64) ? ((m >> (-d)) & (unsigned long long)kFixMask) : 0ull;
-        f.c[j] += neg ? -(long long)v : (long long)v;
+    unsigned long long lo = 0ull, hi = 0ull;
+    if (sh >= 64) hi = m << (sh - 64);
+    else if (sh > 0) { lo = m << sh; hi = m >> (64 - sh); }
+    else if (sh > -64) lo = m >> (-sh);
+    const unsigned long long k = (unsigned long long)kFixMask;
+    long long c0 = (long long)(lo & k), c1 = (long long)(((lo >> 42) | (hi << 22)) & k), c2 = (long long)(hi >> 20);
+    if (neg) {
+        c0 = -c0;
+        c1 = -c1;
+        c2 = -c2;
     }
+    f.c[0] += c0;
+    f.c[1] += c1;
+    f.c[2] += c2;
 }
 
 __device__ __forceinline__ void fix_add(Fix3& f, float t)
@@ -491,6 +498,23 @@ __device__ __forceinline__ double fix_value(Fix3 f)
     return neg ? -mag : mag;
 }
 
+// Whether the exact sum s is below e: Eq. (Paccept) as dA < -log u, decided
+// in the fixed point (e truncated like the terms; -log u is a multiple of
+// 2^-64 whenever u < 0.9997).  A NaN or +inf sum rejects, -inf accepts.
+__device__ __forceinline__ bool fix_less(Fix3 s, double e)
+{
+    if (s.flags) return s.flags == 2ull;
+    Fix3 t;
+    fix_zero(t);
+    fix_add(t, e);
+    if (t.flags) return t.flags == 1ull;
+    fix_normalize(s);
+    fix_normalize(t);
+    if (s.c[2] != t.c[2]) return s.c[2] < t.c[2];
+    if (s.c[1] != t.c[1]) return s.c[1] < t.c[1];
+    return s.c[0] < t.c[0];
+}
+
 // CTA sum of every thread's Fix3 (one CTA barrier inside), carries
 // normalised; valid in thread 0.
 template <int NT>
@@ -507,11 +531,13 @@ __device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
     __syncthreads();
     Fix3 t;
     fix_zero(t);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NT / 32; ++k) {
+    if (threadIdx.x < 32) {
+        if (lane < NT / 32) t = wfix[lane];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) t.c[j] += wfix[k].c[j];
-            t.flags |= wfix[k].flags;
+        for (int off = NT / 64; off > 0; off >>= 1) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t.c[j] += __shfl_xor_sync(0xffffffffu, t.c[j], off);
+            t.flags |= __shfl_xor_sync(0xffffffffu, t.flags, off);
         }
         fix_normalize(t);
     }
@@ -544,14 +570,14 @@ struct GridSync {
         if (f.flags) asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(acc + 3), "l"(f.flags) : "memory");
     }
     // thread 0, after the barrier
-    __device__ __forceinline__ double total(const Ctx& c, unsigned slot, const Fix3*) const
+    __device__ __forceinline__ Fix3 total(const Ctx& c, unsigned slot, const Fix3*) const
     {
         const unsigned long long* acc = (const unsigned long long*)c.partials + 4 * slot;
         Fix3 t;
 #pragma unroll
         for (int j = 0; j < 3; ++j) t.c[j] = (long long)__ldcg(acc + j);
         t.flags = __ldcg(acc + 3);
-        return fix_value(t);
+        return t;
     }
     // thread 0, after reading the total of `slot`: clear the previous slot
     __device__ __forceinline__ void recycle(const Ctx& c, unsigned slot) const
@@ -573,7 +599,7 @@ struct BlockSync {
     }
     __device__ __forceinline__ bool arrive_wait(const Ctx&, unsigned*) const { return true; }
     __device__ __forceinline__ void publish(const Ctx&, unsigned, const Fix3& f, Fix3* cta) const { *cta = f; }
-    __device__ __forceinline__ double total(const Ctx&, unsigned, const Fix3* cta) const { return fix_value(*cta); }
+    __device__ __forceinline__ Fix3 total(const Ctx&, unsigned, const Fix3* cta) const { return *cta; }
     __device__ __forceinline__ void recycle(const Ctx&, unsigned) const {}
     __device__ __forceinline__ bool lead() const { return true; }
 };
@@ -645,12 +671,12 @@ __device__ __forceinline__ void apply_move(R* q, const SweepShared<R, NT>& sh, i
         if (j == l || (j == 7 && l == 6)) q[j] = sh.q_new[l][j];
 }
 
-// Decision of move l on the total change of action v: Eq. (Paccept) as
-// dA < -log u (NaN compares false).  One thread.
+// Decision of move l on the exact total change of action: Eq. (Paccept) as
+// dA < -log u (fix_less).  One thread.
 template <class R, int NT>
-__device__ __forceinline__ void decide(SweepShared<R, NT>& sh, int l, double v)
+__device__ __forceinline__ void decide(SweepShared<R, NT>& sh, int l, const Fix3& v)
 {
-    const int acc = (v < sh.elog[l]) ? 1 : 0;
+    const int acc = fix_less(v, sh.elog[l]) ? 1 : 0;
     if (acc) {
         sh.p[l] = sh.pnew[l];
         sh.q_cur[l] = sh.q_new[l][l];
