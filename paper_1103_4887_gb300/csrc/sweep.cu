@@ -385,28 +385,6 @@ __device__ __forceinline__ R trap_term(const Ctx& c, const Coef<R>& k, int64_t n
     return t;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return v;
-}
-
-// Fixed-order CTA sum of NT threads; result valid in thread 0.
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* wsum)
-{
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) wsum[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NT / 32; ++k) t += wsum[k];
-    return t;
-}
-
 // ---- exact sums of parameter-move terms ---------------------------------------
 // A term t enters as the integer T = t 2^64 truncated toward zero (|t| < 2^62;
 // terms below 2^-64 vanish), held in three signed 64-bit chunks of 42 bits,
