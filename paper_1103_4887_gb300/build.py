@@ -17,7 +17,7 @@ LIB = os.path.join(BUILD, "libpimc.so")
 ROOT = os.path.dirname(HERE)
 
 CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu", "noalloc.cu", "hmc.cu"]
-HEADERS = ["device.cuh", "internal.h", "stats.cuh", "scheme.cuh"]
+HEADERS = ["device.cuh", "internal.h", "stats.cuh", "scheme.cuh", "reduce.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -15,41 +15,10 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 #include "stats.cuh"
 
 namespace pimc {
-
-template <int K>
-__device__ void hmc_grid_sums(const Ctx& c, double (&v)[K], double* out, double (*wsum)[kBlock / 32], int* last)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double w = v[k];
-        for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
-        if (lane == 0) wsum[k][wid] = w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (int j = 0; j < kBlock / 32; ++j) t += wsum[k][j];
-            c.red[(int64_t)blockIdx.x * 8 + k] = t;
-        }
-        __threadfence();
-        *last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (*last && threadIdx.x == 0) {
-        __threadfence();
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(&c.red[(int64_t)i * 8 + k]);
-            out[k] = t;
-        }
-        *c.ticket = 0u;
-    }
-}
 
 // Q = current state (FP64), P_j = z_j / sqrt(invm_j) (fixed parameters: 0),
 // K0 = 1/2 sum P^2 invm; step jitter eps (0.8 + 0.4 u') and -log u of the
@@ -82,7 +51,7 @@ __global__ void __launch_bounds__(kBlock) hmc_begin_kernel(Ctx c, HmcScalars* hs
         v[0] += 0.5 * pj * pj * invm[j];
     }
     double k0[1];
-    hmc_grid_sums<1>(c, v, k0, wsum, &last);
+    grid_sums_last_block<1>(c, v, k0, wsum, &last);
     if (last && threadIdx.x == 0) {
         hs->K0 = k0[0];
         const uint4 w = draw_block(seed, c.chain, traj, 0u, kKindHmcAcc, 0u);
@@ -133,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) hmc_end_kernel(Ctx c, HmcScalars* hs, 
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < nq; j += (int64_t)gridDim.x * kBlock)
         v[0] += 0.5 * P[j] * P[j] * invm[j];
     double k1[1];
-    hmc_grid_sums<1>(c, v, k1, wsum, &last);
+    grid_sums_last_block<1>(c, v, k1, wsum, &last);
     if (last && threadIdx.x == 0) {
         hs->K1 = k1[0];
         const double dH = (hs->A1[0] + k1[0]) - (hs->A0[0] + hs->K0);

@@ -3,6 +3,7 @@
 // through the RK4 map (stages recomputed), and path layout conversion.
 #include "device.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 #include "scheme.cuh"
 
 namespace pimc {
@@ -33,47 +34,6 @@ __global__ void refresh_cache_kernel(Ctx c)
     cache_value<Model, R>(c, kc, x, pr, n, f);
     R* F = (R*)c.F[c.st->fidx];
     for (int a = 0; a < D; ++a) F[a * c.ldf + n] = f[a];
-}
-
-template <class T> __device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return v;
-}
-
-// K FP64 sums: per-CTA fixed-order sums into c.red[cta*8+k]; the last CTA to
-// arrive adds the CTA sums in CTA order and writes out[k].  Deterministic.
-template <int K>
-__device__ void grid_sums_last_block(const Ctx& c, double (&v)[K], double* out, double (*wsum)[kBlock / 32],
-                                     int* last)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double w = warp_sum_d<double>(v[k]);
-        if (lane == 0) wsum[k][wid] = w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (int j = 0; j < kBlock / 32; ++j) t += wsum[k][j];
-            c.red[(int64_t)blockIdx.x * 8 + k] = t;
-        }
-        __threadfence();
-        *last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (*last && threadIdx.x == 0) {
-        __threadfence();
-        for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(&c.red[(int64_t)i * 8 + k]);
-            out[k] = t;
-        }
-        *c.ticket = 0u;
-    }
 }
 
 // Path element (a, n) from either the handle's storage or a dense FP64 array.
