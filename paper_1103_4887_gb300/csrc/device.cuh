@@ -118,17 +118,17 @@ template <class R> __device__ __forceinline__ void psi_frac(R u, R& num, R& den)
         den = -Num<R>::exm1(-u);
     }
 }
-// d psi/du = (1 - e^{-u} - u e^{-u}) / (1 - e^{-u})^2; series
-// 1/2 + u/6 - u^3/180 + u^5/5040 below the cut.
-template <class R> __device__ __forceinline__ R dpsi(R u)
+// d psi/du = (1 - e^{-u} - u e^{-u}) / (1 - e^{-u})^2, series
+// 1/2 + u/6 - u^3/180 + u^5/5040 below the cut.  Formed from em = 1 - e^{-u},
+// the denominator psi_frac already computed (|u| >= dpsi_cut > psi_cut, so
+// psi_frac took that branch): e^{-u} = 1 - em, no second exponential.
+template <class R> __device__ __forceinline__ R dpsi_em(R u, R em)
 {
     if (fabs(u) < Num<R>::dpsi_cut) {
         const R u2 = u * u;
         return R(0.5) + u * (R(1.0 / 6.0) + u2 * (R(-1.0 / 180.0) + u2 * R(1.0 / 5040.0)));
     }
-    const R em = -Num<R>::exm1(-u);
-    const R e = Num<R>::ex(-u);
-    return Num<R>::div(em - u * e, em * em);
+    return Num<R>::div(em - u * (R(1) - em), em * em);
 }
 
 // Hodgkin-Huxley (1952) in the modern convention, conductance form:
@@ -152,13 +152,19 @@ template <class R> struct HH {
     // quotients share one reciprocal.  Divisions by constants are products.
     static __device__ __forceinline__ void rates(R V, R a[3], R b[3])
     {
+        R dm, dn;
+        rates_den(V, a, b, dm, dn);
+    }
+    // rates, and the psi denominators 1 - e^{-u} of alpha_m and alpha_n
+    static __device__ __forceinline__ void rates_den(R V, R a[3], R b[3], R& dm, R& dn)
+    {
         const R t = V + R(65);
         const R E = Num<R>::ex(t * R(-0.0125));
         const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
         b[2] = R(0.125) * E;
         a[1] = R(0.07) * E4;
         b[0] = R(4) * Num<R>::ex(t * R(-1.0 / 18.0));
-        R nm, dm, nn, dn;
+        R nm, nn;
         psi_frac<R>((V + R(40)) * R(0.1), nm, dm);
         psi_frac<R>((V + R(55)) * R(0.1), nn, dn);
         const R dh = R(1) + E8 * R(20.085536923187668);  // e^3
@@ -183,15 +189,15 @@ template <class R> struct HH {
     // gx += J_x^T w, gp += J_p^T w (gp indexed like p: 7 entries)
     static __device__ __forceinline__ void rhs_vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp)
     {
-        R a[3], b[3];
-        rates(x[0], a, b);
+        R a[3], b[3], em_m, em_n;
+        rates_den(x[0], a, b, em_m, em_n);
         const R V = x[0], m = x[1], h = x[2], n = x[3];
         R da[3], db[3];
-        da[0] = dpsi<R>((V + R(40)) * R(0.1)) * R(0.1);
+        da[0] = dpsi_em<R>((V + R(40)) * R(0.1), em_m) * R(0.1);
         db[0] = b[0] * R(-1.0 / 18.0);
         da[1] = a[1] * R(-0.05);
         db[1] = b[1] * (R(1) - b[1]) * R(0.1);
-        da[2] = dpsi<R>((V + R(55)) * R(0.1)) * R(0.01);
+        da[2] = dpsi_em<R>((V + R(55)) * R(0.1), em_n) * R(0.01);
         db[2] = b[2] * R(-0.0125);
         const R gNa = q[0], gK = q[1], gL = q[2], ENa = q[3], EK = q[4], EL = q[5], iC = q[7];
         const R m3h = m * m * m * h, n4 = n * n * n * n;
@@ -382,11 +388,12 @@ __device__ __forceinline__ void rk4_map(const R* x, const R* p, R I, R dt, R* f)
 }
 
 // Reverse mode through the RK4 step: the stage states are recomputed from x
-// (nothing stored), then the cotangent w of f is pulled back stage by stage.
-// Also returns f itself.  gx, gp are accumulated into.
-template <class Model, class R>
-__device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, const R* w, R* f,
-                                        R* gx, R* gp)
+// (nothing stored); once f = f(x) is formed, cot(f, w) fills the cotangent w
+// of f (e.g. from the residual x_{n+1} - f), which is then pulled back stage
+// by stage -- one forward pass serves both the residual and the adjoint.
+// gx, gp are accumulated into; w is left holding the cotangent.
+template <class Model, class R, class Cot>
+__device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, Cot cot, R* w, R* gx, R* gp)
 {
     constexpr int D = Model::D;
     R k1[D], k2[D], k3[D], k4[D], x2[D], x3[D], x4[D];
@@ -400,9 +407,11 @@ __device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, const
 #pragma unroll
     for (int a = 0; a < D; ++a) x4[a] = x[a] + dt * k3[a];
     Model::rhs(x4, p, I, k4);
+    R f[D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
         f[a] = x[a] + dt / R(6) * (((k1[a] + R(2) * k2[a]) + R(2) * k3[a]) + k4[a]);
+    cot(f, w);
 
     R b1[D], b2[D], b3[D], b4[D], u[D];
 #pragma unroll

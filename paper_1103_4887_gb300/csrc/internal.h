@@ -14,6 +14,7 @@ constexpr int kMaxGrid = 4096;       // upper bound on CTAs of a launch (partial
 constexpr int kMaxSel = 64;          // histogram components
 constexpr int kMaxBins = 4096;
 constexpr int kDrawChunk = 4096;   // sweeps a launch (the parameter-draw buffer's capacity)
+constexpr int kRedStride = 16;     // per-CTA double slots of the single-pass reductions' scratch
 
 // Scalar sampler state living in device memory.  The sweep kernel keeps a
 // per-CTA copy in shared memory; every CTA evolves it identically (same draws,
@@ -50,7 +51,7 @@ struct Ctx {
     unsigned long long* flags;    // [2][kMaxGrid] neighbour epoch flags of the sweep
     uint64_t ep0;                 // epoch of the sweep before this launch's first (flags only grow)
     unsigned* ticket;             // last-block counter of single-pass reductions
-    double* red;                  // [kMaxGrid * 8] per-CTA partials of single-pass reductions
+    double* red;                  // [2][kMaxGrid * kRedStride] per-CTA partials of single-pass reductions
     const double* pdraw;          // [kDrawChunk][NP][2] parameter draws of a resident launch (z, -log u)
     double *S1, *S2, *shift;      // [D*(M+1) + NP] running shifted sums (FP64)
     double *R1, *R2;              // [(D+1)*M] residual sums: eps_{n+1,a} at a*M+n, delta_n at D*M+n-1
@@ -75,13 +76,21 @@ struct HmcScalars {
     double K0, K1, dH, E, eps;    // kinetic energies, dH, -log u, jittered step
     int oob, accept;
     unsigned long long n_acc, n_traj;
+    // parameter momenta by step parity: leapfrog step k writes P_p(k - 1/2)
+    // to pp[k & 1] while its CTAs read P_p(k - 3/2) from the other row
+    double pp[2][kMaxParams];
 };
 struct HmcBuffers {
     HmcScalars* hs;
-    double *Q, *P, *g, *invm;     // [D*(M+1) + NP] each: positions, momenta, gradient, inverse mass
+    // [D*(M+1) + NP] each: positions (two buffers), momenta, the trajectory's
+    // eps invm, inverse mass; site entries of Q, Q2, P, EM hold a double, or
+    // in the FP32-mixed form a float pair hi + lo (parameter entries: double)
+    double *Q, *Q2, *P, *EM, *invm;
 };
+// pdl: launch the kernels after the first with programmatic dependent launch
+// (as captured into the trajectory's graph).
 cudaError_t launch_hmc_trajectory(int model, int prec, const Ctx& c, const HmcBuffers& b, int n_leap, double eps,
-                                  uint64_t seed, cudaStream_t s);
+                                  uint64_t seed, bool pdl, cudaStream_t s);
 
 template <class R> constexpr int prec_of();
 template <> constexpr int prec_of<double>() { return 0; }

@@ -127,12 +127,15 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(Ctx c, const double* Xe, c
             }
             for (int l = 0; l < NP; ++l) vp[l] -= 0.5 * c.dt * (double)gpl[l];
         } else if (n < c.M) {
-            R w[D], f[D], fx[D], gpl[kMaxP];
+            R w[D], x1[D], gpl[kMaxP];
             for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
-            // f(x_n) first, for the residual that seeds the cotangent
-            rk4_map<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), fx);
-            for (int a = 0; a < D; ++a) w[a] = R(beta * c.Rf[a]) * (path_at<R>(c, Xe, a, n + 1) - fx[a]);
-            rk4_vjp<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt), w, f, gx, gpl);
+            for (int a = 0; a < D; ++a) x1[a] = path_at<R>(c, Xe, a, n + 1);
+            // the residual x_{n+1} - f(x_n) seeds the cotangent
+            rk4_vjp<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt),
+                              [&](const R* f, R* wv) {
+                                  for (int a = 0; a < D; ++a) wv[a] = R(beta * c.Rf[a]) * (x1[a] - f[a]);
+                              },
+                              w, gx, gpl);
             for (int a = 0; a < D; ++a) {
                 own[a] -= (double)gx[a];
                 atomicAdd(&gX[a * ld + n + 1], (double)w[a]);

@@ -9,16 +9,18 @@
 
 namespace pimc {
 
-__device__ __forceinline__ double warp_sum_fp64(double v)
+// Fixed-order tree sum over a warp (lane 0 holds the result).
+template <class T> __device__ __forceinline__ T warp_sum(T v)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     return v;
 }
+__device__ __forceinline__ double warp_sum_fp64(double v) { return warp_sum<double>(v); }
 
 // v: this thread's K partial sums.  out[k] (written by thread 0 of the last
 // CTA) receives the grid totals; *last tells the caller which CTA that is.
-// Uses c.red[cta * 8 + k] (K <= 8) and c.ticket.
+// Uses c.red[cta * kRedStride + k] (K <= kRedStride) and c.ticket.
 template <int K>
 __device__ void grid_sums_last_block(const Ctx& c, double (&v)[K], double* out, double (*wsum)[kBlock / 32],
                                      int* last)
@@ -34,7 +36,7 @@ __device__ void grid_sums_last_block(const Ctx& c, double (&v)[K], double* out, 
         for (int k = 0; k < K; ++k) {
             double t = 0.0;
             for (int j = 0; j < kBlock / 32; ++j) t += wsum[k][j];
-            c.red[(int64_t)blockIdx.x * 8 + k] = t;
+            c.red[(int64_t)blockIdx.x * kRedStride + k] = t;
         }
         __threadfence();
         *last = (atomicAdd(c.ticket, 1u) == gridDim.x - 1);
@@ -47,7 +49,7 @@ __device__ void grid_sums_last_block(const Ctx& c, double (&v)[K], double* out, 
         for (int k = 0; k < K; ++k) t[k] = 0.0;
         for (unsigned i = threadIdx.x; i < gridDim.x; i += kBlock) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) t[k] += __ldcg(&c.red[(int64_t)i * 8 + k]);
+            for (int k = 0; k < K; ++k) t[k] += __ldcg(&c.red[(int64_t)i * kRedStride + k]);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {

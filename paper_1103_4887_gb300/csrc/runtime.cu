@@ -25,6 +25,7 @@ struct pimc_handle_s {
     int device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;  // private stream the HMC graph is captured on
     // device buffers (sized for FP64 elements; FP32 storage uses the first half)
     void* X = nullptr;
     void* F[2] = {nullptr, nullptr};
@@ -231,10 +232,11 @@ void free_all(pimc_t h)
     void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar, h->flags,
                     h->ticket, h->red, h->pdraw, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
                     h->dense, h->small, h->y64, h->I64, h->trace, h->R1, h->R2, h->hmc.hs, h->hmc.Q, h->hmc.P,
-                    h->hmc.g, h->hmc.invm};
+                    h->hmc.Q2, h->hmc.EM, h->hmc.invm};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->hmc_exec) cudaGraphExecDestroy(h->hmc_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
 // clear statistics, counters and windows (sweep counter and beta follow the schedule)
@@ -306,7 +308,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         {(void**)&h->bar, sizeof(unsigned) * 4},
         {(void**)&h->flags, sizeof(unsigned long long) * 2 * kMaxGrid},
         {(void**)&h->ticket, sizeof(unsigned) * 4},
-        {(void**)&h->red, sizeof(double) * 8 * kMaxGrid},
+        {(void**)&h->red, sizeof(double) * 2 * kRedStride * kMaxGrid},
         {(void**)&h->pdraw, sizeof(double) * 2 * kMaxParams * kDrawChunk},
         {(void**)&h->S1, sizeof(double) * nc},
         {(void**)&h->S2, sizeof(double) * nc},
@@ -750,7 +752,8 @@ int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv
         CK(h, cudaMalloc(&h->hmc.hs, sizeof(HmcScalars)));
         CK(h, cudaMalloc(&h->hmc.Q, sizeof(double) * nq));
         CK(h, cudaMalloc(&h->hmc.P, sizeof(double) * nq));
-        CK(h, cudaMalloc(&h->hmc.g, sizeof(double) * nq));
+        CK(h, cudaMalloc(&h->hmc.Q2, sizeof(double) * nq));
+        CK(h, cudaMalloc(&h->hmc.EM, sizeof(double) * nq));
         CK(h, cudaMalloc(&h->hmc.invm, sizeof(double) * nq));
         CK(h, cudaMemset(h->hmc.hs, 0, sizeof(HmcScalars)));
     }
@@ -780,26 +783,25 @@ int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv
             cudaGraphExecDestroy(h->hmc_exec);
             h->hmc_exec = nullptr;
         }
-        if (h->stream) {
-            cudaGraph_t graph = nullptr;
-            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = launch_hmc_trajectory(h->model, h->prec, make_ctx(h), h->hmc, n_leap, eps, seed, h->stream);
-            cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
-            if (e == cudaSuccess) e = e2;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&h->hmc_exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            CK(h, e);
-        }
+        // captured on a private stream (the legacy default stream cannot be
+        // captured) and launched on the handle's stream, whichever that is
+        if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e =
+            launch_hmc_trajectory(h->model, h->prec, make_ctx(h), h->hmc, n_leap, eps, seed, true, h->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->hmc_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        CK(h, e);
         h->hmc_leap = n_leap;
         h->hmc_eps = eps;
         h->hmc_seed = seed;
         h->hmc_prec = h->prec;
         h->hmc_version = h->ctx_version;
     }
-    for (int64_t t = 0; t < n_traj; ++t) {
-        if (h->hmc_exec) CK(h, cudaGraphLaunch(h->hmc_exec, h->stream));
-        else CK(h, launch_hmc_trajectory(h->model, h->prec, make_ctx(h), h->hmc, n_leap, eps, seed, h->stream));
-    }
+    for (int64_t t = 0; t < n_traj; ++t) CK(h, cudaGraphLaunch(h->hmc_exec, h->stream));
     if (n_accepted) {
         HmcScalars hs;
         CK(h, cudaMemcpyAsync(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost, h->stream));

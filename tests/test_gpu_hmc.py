@@ -5,7 +5,8 @@ the closed-form linear-Gaussian posterior.
   state; accept decisions must agree (a differing decision must sit within
   1e-9 of its threshold) and accepted end points must agree to the leapfrog's
   rounding (FP64).
-* T-LG: means and variances of GPU HMC chains match the closed form.
+* T-LG: means and variances of GPU HMC chains match the closed form (FP64
+  and FP32-mixed).
 """
 import numpy as np
 import pytest
@@ -60,14 +61,17 @@ def test_hmc_replay_against_oracle(model):
     assert agree >= 5  # the chain moves
 
 
-def test_hmc_T_LG_closed_form():
+@pytest.mark.parametrize("precision", ["fp64", "fp32mixed"])
+def test_hmc_T_LG_closed_form(precision):
+    """Also the FP32-mixed form, whose positions and momenta are float pairs
+    (hi + lo) with FP32 gradients: its chains target the same posterior."""
     prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
     L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True)
     mu, cov = lgc.posterior(L, r, w)
     inv_mass = np.diag(cov).copy()
     means, vars_ = [], []
     for k in range(8):
-        g = pimc.Sampler.from_problem(prob)
+        g = pimc.Sampler.from_problem(prob, precision=pimc.FP64 if precision == "fp64" else pimc.FP32_MIXED)
         g.set_chain(k)
         g.set_schedule(n_init=200, n_skip=1)
         nacc = g.hmc(200 + 6000, 16, 0.2, inv_mass, seed=9)
