@@ -189,6 +189,23 @@ def run_profile_case(args):
     print("profile case done")
 
 
+def run_profile_hmc(args):
+    """Three whole-path HMC trajectories (L = 20) in each precision on the
+    ESS workload (HH, M = 16384, all 7 parameters free; no timing); the case
+    the ncu captures of the leapfrog kernel use."""
+    from paper_1103_4887_gb300 import pimc, synth
+    prob = synth.hh_problem(16384, data_seed=0, free="all")
+    for prec in (pimc.FP32_MIXED, pimc.FP64):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
+        s.set_path(prob.X_true)
+        s.set_schedule(n_init=10 ** 9, n_skip=1)
+        n = s.hmc(3, 20, 0.005, None, seed=SEED)
+        print(json.dumps({"precision": prec, "accepted": n}))
+        s.close()
+    print("profile case done")
+
+
 def _peak_fp32_tflops(n_sm, sm_mhz):
     t_map = max(FP32_OPS_PER_MAP / (n_sm * 128 * sm_mhz * 1e6), MUFU_OPS_PER_MAP / (n_sm * 16 * sm_mhz * 1e6))
     return FLOP_PER_MAP / t_map / 1e12
@@ -482,6 +499,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--profile", action="store_true",
                     help="no timing: 3 launches of one bench step per precision (a small case for ncu)")
+    ap.add_argument("--profile-hmc", action="store_true",
+                    help="no timing: 3 HMC trajectories per precision on the ESS workload (a small case for ncu)")
     ap.add_argument("--sweep-M", action="store_true",
                     help="observation-length sweep M = 2^10..2^20: site-updates/s and roofline per M, FP32-mixed "
                          "and FP64, with the serial oracle timed on the host for the same M")
@@ -502,6 +521,9 @@ def main():
         return
     if args.profile:
         run_profile_case(args)
+        return
+    if args.profile_hmc:
+        run_profile_hmc(args)
         return
     if args.sweep_M:
         run_sweep_M(args)
