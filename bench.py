@@ -351,7 +351,7 @@ def run_mixed(args):
     from paper_1103_4887_gb300 import diagnostics, pimc, synth
     M = args.M
     prob = synth.hh_problem(M, data_seed=0, free="all")
-    out = {"M": M, "n_free": 7}
+    out = {"M": M, "n_free": 7, "length_scale": scale}
     st = torch.cuda.current_stream()
     # (1) Delta A on the same states and proposals
     X = synth.random_path_near(prob, prob.X_true, 0.5 * prob.sig_x, seed=11)
@@ -421,17 +421,32 @@ def run_mixed(args):
     return out
 
 
-def run_ess(args):
+def _ess_bm(tr, secs, ess_geyer):
+    """Batch-means cross-check of the ESS: var(x) / se_bm^2 per parameter,
+    with about five effective samples a batch (5..30 batches) -- batches
+    shorter than the autocorrelation time would overstate the ESS."""
+    from paper_1103_4887_gb300 import diagnostics
+    n_batches = int(min(30, max(5, np.floor(np.min(ess_geyer) / 5.0))))
+    se = diagnostics.batch_means_se(tr, n_batches)
+    var = tr.var(axis=0, ddof=1)
+    ess = np.where(se > 0, var / np.maximum(se * se, 1e-300), float(tr.shape[0]))
+    return {"ess_batch_means": ess.tolist(), "batch_means_batches": n_batches,
+            "min_ess_batch_means_per_s": float(ess.min() / secs)}
+
+
+def run_ess(args, scale=1):
     """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
-    all 7 parameters free): checkerboard Metropolis in FP32-mixed and FP64, and
-    whole-path HMC (FP64), on the same data.  Chains start at the true path and
-    parameters and adapt during a burn-in, so the figure measures mixing in the
-    posterior, not the approach to it."""
+    all 7 parameters free): checkerboard Metropolis and whole-path HMC, each
+    in FP32-mixed and FP64, on the same data.  Chains start at the true path
+    and parameters and adapt during a burn-in, so the figure measures mixing
+    in the posterior, not the approach to it.  scale multiplies the sampling
+    lengths: at scale 1 the slowest parameter gets only a few effective
+    samples (an indicative figure), at 20 some tens."""
     import torch
     from paper_1103_4887_gb300 import diagnostics, pimc, synth
     M = 16384
     prob = synth.hh_problem(M, data_seed=0, free="all")
-    out = {"M": M, "n_free": 7}
+    out = {"M": M, "n_free": 7, "length_scale": scale}
     st = torch.cuda.current_stream()
 
     def timed(fn):
@@ -442,46 +457,57 @@ def run_ess(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
 
-    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 100000),
-                                ("metropolis_fp64", pimc.FP64, 2000, 16000)):
+    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 100000 * scale),
+                                ("metropolis_fp64", pimc.FP64, 2000, 16000 * scale)):
         s = pimc.Sampler.from_problem(prob, precision=prec)
         s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
         s.set_path(prob.X_true)
         s.set_stream(st.cuda_stream)
         s.set_schedule(n_init=burn, n_skip=20, f_acc=0.4, alpha=0.5)
-        s.sweep(burn, SEED, sync=False)
+        burn_secs = timed(lambda: s.sweep(burn, SEED, sync=False))
         s.set_param_trace(n)
         secs = timed(lambda: s.sweep(n, SEED, sync=False))
         s.sync()
         tr = s.param_trace()
         ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
-        out[name] = {"sweeps": n, "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
-                     "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
+        out[name] = {"sweeps": n, "seconds": secs, "burn_in_sweeps": burn, "burn_in_seconds": burn_secs,
+                     "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
+                     "median_ess_per_s": float(np.median(ess) / secs), **_ess_bm(tr, secs, ess),
+                     "mean_p": tr.mean(0).tolist()}
         s.close()
 
     # whole-path HMC: diagonal mass from burn-in variances, step tuned to ~70 %
-    for name, prec, n_traj in (("hmc_fp64", pimc.FP64, 2500), ("hmc_fp32mixed", pimc.FP32_MIXED, 10000)):
+    for name, prec, n_traj in (("hmc_fp64", pimc.FP64, 2500 * scale),
+                               ("hmc_fp32mixed", pimc.FP32_MIXED, 10000 * scale)):
         s = pimc.Sampler.from_problem(prob, precision=prec)
         s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
         s.set_path(prob.X_true)
         s.set_stream(st.cuda_stream)
         s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
-        s.sweep(4000, SEED, sync=False)
+        burn_secs = timed(lambda: s.sweep(4000, SEED, sync=False))
         mean, var, J = s.moments()
         inv_mass = np.where(np.isfinite(var) & (var > 0), var, 1e-12)
         s.set_schedule(n_init=10 ** 9, n_skip=1)
         eps, n_leap = 0.05, 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
         for _ in range(12):
             acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
             eps *= float(np.exp(1.5 * (acc - 0.7)))
+        e1.record(st)
+        torch.cuda.synchronize()
+        burn_secs += e0.elapsed_time(e1) * 1e-3
         s.set_param_trace(n_traj)
         acc_box = {}
         secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
         tr = s.param_trace()
         ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
         out[name] = {"trajectories": n_traj, "n_leap": n_leap, "eps": eps, "accept": acc_box["n"] / n_traj,
-                     "seconds": secs, "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
-                     "median_ess_per_s": float(np.median(ess) / secs), "mean_p": tr.mean(0).tolist()}
+                     "seconds": secs, "burn_in_seconds": burn_secs,
+                     "burn_in": "4000 Metropolis sweeps (mass from their variances) + 120 step-tuning trajectories",
+                     "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
+                     "median_ess_per_s": float(np.median(ess) / secs), **_ess_bm(tr, secs, ess),
+                     "mean_p": tr.mean(0).tolist()}
         s.close()
     return out
 
@@ -514,6 +540,8 @@ def main():
                          "posterior-mean shift in MC standard errors")
     ap.add_argument("--ess", action="store_true",
                     help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
+    ap.add_argument("--ess-scale", type=int, default=20,
+                    help="sampling lengths of --ess relative to the short runs of the default line (which use 1)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -529,7 +557,7 @@ def main():
         run_sweep_M(args)
         return
     if args.ess:
-        print(json.dumps(run_ess(args)), flush=True)
+        print(json.dumps(run_ess(args, scale=args.ess_scale)), flush=True)
         return
     if args.mixed:
         print(json.dumps(run_mixed(args)), flush=True)
@@ -658,6 +686,11 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
             "kernel": kname, "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
+    if traffic is not None:  # the memory side of the same launch, against the copy peak
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roof["dram_gbs"] = traffic / (ms_per_step * 1e-3) / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm
+        roof["dram_peak_gbs"] = hbm
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -675,8 +708,11 @@ def main():
             extras["mixed"] = {"error": repr(e)}
         try:
             ess = run_ess(args)
-            extras["ess"] = {k: ({kk: v[kk] for kk in ("min_ess_per_s", "median_ess_per_s", "seconds")}
-                                 if isinstance(v, dict) else v) for k, v in ess.items()}
+            keep = ("min_ess_per_s", "median_ess_per_s", "min_ess_batch_means_per_s", "seconds", "burn_in_seconds")
+            extras["ess"] = {k: ({kk: v[kk] for kk in keep if kk in v} if isinstance(v, dict) else v)
+                             for k, v in ess.items()}
+            extras["ess"]["note"] = ("short runs, indicative only: the slowest parameters' autocorrelation "
+                                     "times exceed these runs, which overstates ESS; bench.py --ess runs 20x longer")
         except Exception as e:
             extras["ess"] = {"error": repr(e)}
 
@@ -690,7 +726,9 @@ def main():
                            "grid_block": grid_block, "form": form},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk.rows),
-                "steady_state": steady, "fp64": fp64}
+                "steady_state": steady, "fp64": fp64,
+                "rk4_maps_per_s": world * maps * NSKIP / (ms_per_step * 1e-3),
+                "param_moves_per_s": world * n_free * NSKIP / (ms_per_step * 1e-3)}
         line.update(extras)
         print(json.dumps(line))
     if dist is not None:

@@ -621,7 +621,10 @@ static cudaError_t hmc_traj_t(const Ctx& c, const HmcBuffers& b, int n_leap, dou
     int64_t T = (c.M + 1 + sms - 1) / (sms > 0 ? sms : 1);
     T = T < 1 ? 1 : (T > kBlock - 1 ? kBlock - 1 : T);
     const int64_t ntile = (c.M + 1 + T - 1) / T;
-    const unsigned gl = (unsigned)(ntile < kMaxGrid ? ntile : kMaxGrid);
+    // at most two CTAs an SM (what the registers allow); beyond, CTAs stride
+    // over tiles -- every CTA reads all CTAs' parameter-gradient sums
+    const int64_t gmax = 2 * (int64_t)(sms > 0 ? sms : 1) < kMaxGrid ? 2 * (int64_t)(sms > 0 ? sms : 1) : kMaxGrid;
+    const unsigned gl = (unsigned)(ntile < gmax ? ntile : gmax);
     // The FP64 step is bound by the FP64 pipe: a next step made resident early
     // (programmatic launch) would share SMs with the running one and leave
     // some SMs with two CTAs of it, which then take twice as long -- so only

@@ -26,9 +26,17 @@ def _oracle(prob):
     return ch
 
 
-@pytest.mark.parametrize("model", ["lg", "hh", "lg_trap"])
+@pytest.mark.parametrize("model", ["lg", "hh", "lg_trap", "hh_many_tiles"])
 def test_hmc_replay_against_oracle(model):
-    if model.startswith("lg"):
+    n_traj = 30
+    if model == "hh_many_tiles":
+        # 40 001 sites: more tiles than the leapfrog kernel's CTAs (two an SM),
+        # so CTAs stride over tiles; a few trajectories keep the oracle quick
+        prob = synth.hh_problem(40000, data_seed=4, free=("gNa", "gK", "gL"))
+        inv_mass = np.concatenate([np.tile([5e-3, 5e-5, 5e-5, 5e-5], (prob.M + 1, 1)).T.ravel(),
+                                   1e-3 * np.abs(prob.p_init)])
+        eps, n_leap, n_traj = 2e-3, 4, 4  # small steps from the truth: accepted trajectories
+    elif model.startswith("lg"):
         prob = synth.lingauss_problem(M=10, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
         prob.scheme = 1 if model == "lg_trap" else 0
         L, r, w = lgc.system(prob.M, prob.dt, prob.Rm, prob.Rf, prob.y, prob.I, p_free=True, scheme=prob.scheme)
@@ -41,9 +49,12 @@ def test_hmc_replay_against_oracle(model):
                                    1e-2 * np.abs(prob.p_init)])
         eps, n_leap = 0.1, 8
     g = pimc.Sampler.from_problem(prob)
+    if model == "hh_many_tiles":
+        g.set_path(prob.X_true)
+        g.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
     o = _oracle(prob)
     agree = 0
-    for t in range(30):
+    for t in range(n_traj):
         X0, p0 = g.state()
         o.set_path(X0)
         o.set_params(p0, prob.lo, prob.hi, prob.free)
@@ -58,7 +69,7 @@ def test_hmc_replay_against_oracle(model):
         scale = np.maximum(1.0, np.abs(Xo))
         assert np.all(np.abs(Xg - Xo) <= 1e-9 * scale), t
         assert np.all(np.abs(pg - po) <= 1e-9 * np.maximum(1.0, np.abs(po))), t
-    assert agree >= 5  # the chain moves
+    assert agree >= (5 if n_traj >= 30 else 1)  # the chain moves
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32mixed"])
