@@ -150,60 +150,6 @@ __global__ void __launch_bounds__(kBlock) hmc_begin_kernel(Ctx c, HmcScalars* hs
     }
 }
 
-// Model term k of the action (x_k -> x_{k+1}, beta = 1): its residual e, the
-// cotangent it sends to x_k (own) and to x_{k+1} (nxt), and its dA/dp (gp).
-// RK4: e = x_{k+1} - f(x_k), w = Rf . e, own = -J_x f^T w, nxt = w,
-// gp = -J_p f^T w.  Trapezoid: e = x_{k+1} - x_k - dt/2 (F_{k+1} + F_k),
-// w = Rf . e, own = -w - dt/2 J_k^T w, nxt = w - dt/2 J_{k+1}^T w,
-// gp = -dt/2 (J_p F_k + J_p F_{k+1})^T w.
-template <class Model, class R>
-__device__ __forceinline__ void term_adjoint(const Ctx& c, const Coef<R>& kc, const R* x, const R* x1, const R* pr,
-                                             R In, R In1, R* e, R* own, R* nxt, R* gp)
-{
-    constexpr int D = Model::D;
-    R jp[kMaxP];
-#pragma unroll
-    for (int l = 0; l < kMaxP; ++l) jp[l] = R(0);
-    if (c.scheme == kSchemeRK4) {
-        R gx[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) gx[a] = R(0);
-        rk4_vjp<Model, R>(x, pr, In, kc.dt,
-                          [&](const R* f, R* w) {
-#pragma unroll
-                              for (int a = 0; a < D; ++a) {
-                                  e[a] = x1[a] - f[a];
-                                  w[a] = kc.Rf[a] * e[a];
-                              }
-                          },
-                          nxt, gx, jp);
-#pragma unroll
-        for (int a = 0; a < D; ++a) own[a] = -gx[a];
-#pragma unroll
-        for (int l = 0; l < kMaxP; ++l) gp[l] = -jp[l];
-    } else {
-        R F0[D], F1[D], w[D], g0[D], g1[D];
-        Model::rhs(x, pr, In, F0);
-        Model::rhs(x1, pr, In1, F1);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            e[a] = x1[a] - x[a] - R(0.5) * kc.dt * (F1[a] + F0[a]);
-            w[a] = kc.Rf[a] * e[a];
-            g0[a] = R(0);
-            g1[a] = R(0);
-        }
-        Model::rhs_vjp(x, pr, In, w, g0, jp);
-        Model::rhs_vjp(x1, pr, In1, w, g1, jp);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            own[a] = -w[a] - R(0.5) * kc.dt * g0[a];
-            nxt[a] = w[a] - R(0.5) * kc.dt * g1[a];
-        }
-#pragma unroll
-        for (int l = 0; l < kMaxP; ++l) gp[l] = -(R(0.5) * kc.dt) * jp[l];
-    }
-}
-
 // Leapfrog step k (0..L) fused with the adjoint, in gather form: a CTA owns
 // T <= kBlock - 1 sites n0..n0+T-1 a tile and thread i <= T evaluates model
 // term n0 - 1 + i (thread 0 recomputes the term of the tile before, whose
@@ -393,7 +339,7 @@ __global__ void __launch_bounds__(kBlock) hmc_leap_kernel(Ctx c, HmcScalars* hs,
                 x[a] = xs[a][i];
                 x1[a] = xs[a][i + 1];
             }
-            term_adjoint<Model, R>(c, kc, x, x1, pr, In, In1, e, own, nxt, gpl);
+            term_adjoint<Model, R>(c, kc, kc.Rf, x, x1, pr, In, In1, e, own, nxt, gpl);
 #pragma unroll
             for (int a = 0; a < D; ++a) nxs[a][i] = nxt[a];
             if (i >= 1) {

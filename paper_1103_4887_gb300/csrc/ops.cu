@@ -1,6 +1,7 @@
 // Whole-path operations outside the sweep: the default initial path, the f
 // cache refresh, the global action (FP64 sums), its gradient by reverse mode
-// through the RK4 map (stages recomputed), and path layout conversion.
+// through the RK4 map (stages recomputed) or the trapezoid rule, and path
+// layout conversion.
 #include "device.cuh"
 #include "internal.h"
 #include "reduce.cuh"
@@ -83,66 +84,69 @@ __global__ void __launch_bounds__(kBlock) action_kernel(Ctx c, const double* Xe,
     }
 }
 
-// Gradient of A_o + beta A_f.  Site n contributes Rm (x_{n,0} - y_n) e_0 and
-// -J_x f(x_n)^T w_n to x_n and w_n = beta Rf . eps_{n+1} to x_{n+1}; each gX
-// element receives exactly two FP64 atomic adds onto zero, whose result does
-// not depend on their order.  dA/dp = -sum_n J_p f(x_n)^T w_n (FP64 sums).
+// Gradient of A_o + beta A_f, in gather form: a CTA owns T <= kBlock - 1
+// sites n0..n0+T-1 a tile and thread i <= T takes model term n0 - 1 + i
+// (term_adjoint; thread 0 recomputes the term of the tile before, whose
+// cotangent reaches x_{n0}).  The owner of site n writes
+// g_n = Rm (x_{n,0} - y_n) e_0 + own_n + nxt_{n-1}, the per-term pieces in R
+// added in FP64 -- every element written once, no atomics, no zeroing pass.
+// dA/dp = sum over terms of their gp, FP64 sums (fixed order).
 template <class Model, class R>
 __global__ void __launch_bounds__(kBlock) grad_kernel(Ctx c, const double* Xe, const double* pe, double beta,
-                                                      double* gX, double* gp)
+                                                      double* gX, double* gp, int T)
 {
     constexpr int D = Model::D, NP = Model::NP;
+    __shared__ R xs[D][kBlock + 1];
+    __shared__ R nxs[D][kBlock];
     __shared__ double wsum[NP][kBlock / 32];
     __shared__ int last;
     __shared__ double res[NP];
-    R pr[kMaxP];
+    R pr[kMaxP], wr[kMaxD];
     Model::prep(pe ? pe : c.st->p, pr);
+    const Coef<R> kc(c);
+#pragma unroll
+    for (int a = 0; a < kMaxD; ++a) wr[a] = R(beta * c.Rf[a]);
+    const R* y = (const R*)c.y;
+    const R* I = (const R*)c.I;
+    const int i = threadIdx.x;
+    const int64_t ld = c.M + 1, ntile = (ld + T - 1) / T;
     double vp[NP];
     for (int l = 0; l < NP; ++l) vp[l] = 0.0;
-    const R* y = (const R*)c.y;
-    const int64_t ld = c.M + 1;
-    for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n <= c.M; n += (int64_t)gridDim.x * kBlock) {
-        R x[D], gx[D];
-        for (int a = 0; a < D; ++a) { x[a] = path_at<R>(c, Xe, a, n); gx[a] = R(0); }
-        double own[D];
-        for (int a = 0; a < D; ++a) own[a] = 0.0;
-        if (n >= 1) own[0] = c.Rm * (double)(x[0] - y[n]);
-        if (n < c.M && c.scheme != kSchemeRK4) {
-            // eps_{n+1} = x_{n+1} - x_n - dt/2 (F_{n+1} + F_n), w = beta Rf . eps:
-            // x_n gets -w - dt/2 J_n^T w, x_{n+1} gets w - dt/2 J_{n+1}^T w
-            const R* I = (const R*)c.I;
-            const R In = I[n], In1 = I[n + 1 < c.M ? n + 1 : c.M - 1];
-            R x1[D], F0[D], F1[D], w[D], g0[D], g1[D], gpl[kMaxP];
-            for (int a = 0; a < D; ++a) { x1[a] = path_at<R>(c, Xe, a, n + 1); g0[a] = R(0); g1[a] = R(0); }
-            for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
-            Model::rhs(x, pr, In, F0);
-            Model::rhs(x1, pr, In1, F1);
-            for (int a = 0; a < D; ++a)
-                w[a] = R(beta * c.Rf[a]) * (x1[a] - x[a] - R(0.5) * R(c.dt) * (F1[a] + F0[a]));
-            Model::rhs_vjp(x, pr, In, w, g0, gpl);
-            Model::rhs_vjp(x1, pr, In1, w, g1, gpl);
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t n0 = tile * T, k = n0 - 1 + i;
+        const bool has_x = i <= T && k >= 0 && k <= c.M, term = i <= T && k >= 0 && k < c.M;
+        const bool owner = i >= 1 && i <= T && k <= c.M;
+        if (has_x)
+            for (int a = 0; a < D; ++a) xs[a][i] = path_at<R>(c, Xe, a, k);
+        if (i == 0 && n0 + T <= c.M)
+            for (int a = 0; a < D; ++a) xs[a][T + 1] = path_at<R>(c, Xe, a, n0 + T);
+        __syncthreads();
+        R own[D];
+        for (int a = 0; a < D; ++a) own[a] = R(0);
+        if (term) {
+            R x[D], x1[D], e[D], nxt[D], gpl[kMaxP];
             for (int a = 0; a < D; ++a) {
-                own[a] += -(double)w[a] - 0.5 * c.dt * (double)g0[a];
-                atomicAdd(&gX[a * ld + n + 1], (double)w[a] - 0.5 * c.dt * (double)g1[a]);
+                x[a] = xs[a][i];
+                x1[a] = xs[a][i + 1];
             }
-            for (int l = 0; l < NP; ++l) vp[l] -= 0.5 * c.dt * (double)gpl[l];
-        } else if (n < c.M) {
-            R w[D], x1[D], gpl[kMaxP];
-            for (int l = 0; l < kMaxP; ++l) gpl[l] = R(0);
-            for (int a = 0; a < D; ++a) x1[a] = path_at<R>(c, Xe, a, n + 1);
-            // the residual x_{n+1} - f(x_n) seeds the cotangent
-            rk4_vjp<Model, R>(x, pr, ((const R*)c.I)[n], R(c.dt),
-                              [&](const R* f, R* wv) {
-                                  for (int a = 0; a < D; ++a) wv[a] = R(beta * c.Rf[a]) * (x1[a] - f[a]);
-                              },
-                              w, gx, gpl);
-            for (int a = 0; a < D; ++a) {
-                own[a] -= (double)gx[a];
-                atomicAdd(&gX[a * ld + n + 1], (double)w[a]);
-            }
-            for (int l = 0; l < NP; ++l) vp[l] -= (double)gpl[l];
+            const R In = I[k];
+            const R In1 = c.scheme == kSchemeRK4 ? R(0) : I[k + 1 < c.M ? k + 1 : c.M - 1];
+            term_adjoint<Model, R>(c, kc, wr, x, x1, pr, In, In1, e, own, nxt, gpl);
+            for (int a = 0; a < D; ++a) nxs[a][i] = nxt[a];
+            if (i >= 1)
+                for (int l = 0; l < NP; ++l) vp[l] += (double)gpl[l];
         }
-        for (int a = 0; a < D; ++a) atomicAdd(&gX[a * ld + n], own[a]);
+        __syncthreads();
+        if (owner) {
+            double g[D];
+            for (int a = 0; a < D; ++a) g[a] = (double)own[a];
+            if (k >= 1) {
+                g[0] = c.Rm * (double)(xs[0][i] - y[k]) + g[0];
+                for (int a = 0; a < D; ++a) g[a] += (double)nxs[a][i - 1];
+            }
+            for (int a = 0; a < D; ++a) gX[a * ld + k] = g[a];
+        }
+        if (tile + gridDim.x < ntile) __syncthreads();  // xs and nxs are reused by the next tile
     }
     grid_sums_last_block<NP>(c, vp, res, wsum, &last);
     if (last && threadIdx.x == 0)
@@ -241,9 +245,15 @@ template <class Model, class R>
 static cudaError_t grad_t(const Ctx& c, const double* Xe, const double* pe, double beta, double* gX, double* gp,
                           cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(gX, 0, sizeof(double) * (size_t)Model::D * (size_t)(c.M + 1), s);
-    if (e != cudaSuccess) return e;
-    grad_kernel<Model, R><<<reduce_grid(c.M), kBlock, 0, s>>>(c, Xe, pe, beta, gX, gp);
+    // sites a tile: spread over every SM while that leaves at most kBlock - 1 a tile
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t T = (c.M + 1 + sms - 1) / (sms > 0 ? sms : 1);
+    T = T < 1 ? 1 : (T > kBlock - 1 ? kBlock - 1 : T);
+    const int64_t ntile = (c.M + 1 + T - 1) / T;
+    const unsigned grid = (unsigned)(ntile < kMaxGrid ? ntile : kMaxGrid);
+    grad_kernel<Model, R><<<grid, kBlock, 0, s>>>(c, Xe, pe, beta, gX, gp, (int)T);
     return cudaGetLastError();
 }
 
