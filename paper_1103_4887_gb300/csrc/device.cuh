@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace pimc {
@@ -118,17 +119,23 @@ template <class R> __device__ __forceinline__ void psi_frac(R u, R& num, R& den)
         den = -Num<R>::exm1(-u);
     }
 }
+// The numerator psi_frac gives: u, or the series below the cut.
+template <class R> __device__ __forceinline__ R psi_num(R u)
+{
+    return fabs(u) < Num<R>::psi_cut ? R(1) + u * (R(0.5) + u * R(1.0 / 12.0)) : u;
+}
 // d psi/du = (1 - e^{-u} - u e^{-u}) / (1 - e^{-u})^2, series
 // 1/2 + u/6 - u^3/180 + u^5/5040 below the cut.  Formed from em = 1 - e^{-u},
 // the denominator psi_frac already computed (|u| >= dpsi_cut > psi_cut, so
-// psi_frac took that branch): e^{-u} = 1 - em, no second exponential.
-template <class R> __device__ __forceinline__ R dpsi_em(R u, R em)
+// psi_frac took that branch), and its reciprocal inv_em: e^{-u} = 1 - em, no
+// second exponential and no division.
+template <class R> __device__ __forceinline__ R dpsi_em(R u, R em, R inv_em)
 {
     if (fabs(u) < Num<R>::dpsi_cut) {
         const R u2 = u * u;
         return R(0.5) + u * (R(1.0 / 6.0) + u2 * (R(-1.0 / 180.0) + u2 * R(1.0 / 5040.0)));
     }
-    return Num<R>::div(em - u * (R(1) - em), em * em);
+    return (em - u * (R(1) - em)) * (inv_em * inv_em);
 }
 
 // Hodgkin-Huxley (1952) in the modern convention, conductance form:
@@ -152,31 +159,57 @@ template <class R> struct HH {
     // quotients share one reciprocal.  Divisions by constants are products.
     static __device__ __forceinline__ void rates(R V, R a[3], R b[3])
     {
-        R dm, dn;
-        rates_den(V, a, b, dm, dn);
+        Cache k;
+        cache_at(V, k);
+        rates_from(V, k, a, b);
     }
-    // rates, and the psi denominators 1 - e^{-u} of alpha_m and alpha_n
-    static __device__ __forceinline__ void rates_den(R V, R a[3], R b[3], R& dm, R& dn)
+    // The transcendental part of the rates at V: E, e^{-t/18}, the psi
+    // denominators dm, dn (1 - e^{-u} of alpha_m, alpha_n) and the shared
+    // reciprocal r = 1/(dm dn dh), dh = 1 + E^8 e^3.  The reverse pass of an
+    // RK4 step reuses the forward pass's (kReuseRates), in FP64 where each
+    // exponential and division is a long FP64 instruction sequence.
+    struct Cache {
+        R E, e18, dm, dn, r;
+    };
+    static constexpr bool kReuseRates = sizeof(R) == sizeof(double);
+    static __device__ __forceinline__ R dh_of(R E)
+    {
+        const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
+        return R(1) + E8 * R(20.085536923187668);  // e^3
+    }
+    static __device__ __forceinline__ void cache_at(R V, Cache& k)
     {
         const R t = V + R(65);
-        const R E = Num<R>::ex(t * R(-0.0125));
-        const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
-        b[2] = R(0.125) * E;
-        a[1] = R(0.07) * E4;
-        b[0] = R(4) * Num<R>::ex(t * R(-1.0 / 18.0));
+        k.E = Num<R>::ex(t * R(-0.0125));
+        k.e18 = Num<R>::ex(t * R(-1.0 / 18.0));
         R nm, nn;
-        psi_frac<R>((V + R(40)) * R(0.1), nm, dm);
-        psi_frac<R>((V + R(55)) * R(0.1), nn, dn);
-        const R dh = R(1) + E8 * R(20.085536923187668);  // e^3
-        const R r = Num<R>::div(R(1), dm * dn * dh);
-        a[0] = nm * (dn * dh * r);
-        a[2] = R(0.1) * nn * (dm * dh * r);
-        b[1] = dm * dn * r;
+        psi_frac<R>((V + R(40)) * R(0.1), nm, k.dm);
+        psi_frac<R>((V + R(55)) * R(0.1), nn, k.dn);
+        k.r = Num<R>::div(R(1), k.dm * k.dn * dh_of(k.E));
+    }
+    static __device__ __forceinline__ void rates_from(R V, const Cache& k, R a[3], R b[3])
+    {
+        const R E2 = k.E * k.E, E4 = E2 * E2;
+        b[2] = R(0.125) * k.E;
+        a[1] = R(0.07) * E4;
+        b[0] = R(4) * k.e18;
+        const R nm = psi_num<R>((V + R(40)) * R(0.1)), nn = psi_num<R>((V + R(55)) * R(0.1));
+        const R dh = dh_of(k.E);
+        a[0] = nm * (k.dn * dh * k.r);
+        a[2] = R(0.1) * nn * (k.dm * dh * k.r);
+        b[1] = k.dm * k.dn * k.r;
     }
     static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F)
     {
+        Cache k;
+        rhs_c(x, q, I, F, k);
+    }
+    // rhs, keeping the rates' transcendental part in k
+    static __device__ __forceinline__ void rhs_c(const R* x, const R* q, R I, R* F, Cache& k)
+    {
         R a[3], b[3];
-        rates(x[0], a, b);
+        cache_at(x[0], k);
+        rates_from(x[0], k, a, b);
         const R V = x[0], m = x[1], h = x[2], n = x[3];
         const R iNa = q[0] * m * m * m * h * (V - q[3]);
         const R iK = q[1] * n * n * n * n * (V - q[4]);
@@ -189,15 +222,25 @@ template <class R> struct HH {
     // gx += J_x^T w, gp += J_p^T w (gp indexed like p: 7 entries)
     static __device__ __forceinline__ void rhs_vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp)
     {
-        R a[3], b[3], em_m, em_n;
-        rates_den(x[0], a, b, em_m, em_n);
+        Cache k;
+        cache_at(x[0], k);
+        rhs_vjp_c(x, q, I, w, gx, gp, k);
+    }
+    // rhs_vjp from the rates' transcendental part at x[0] (no exponential, no
+    // division: 1/dm = r dn dh and 1/dn = r dm dh)
+    static __device__ __forceinline__ void rhs_vjp_c(const R* x, const R* q, R I, const R* w, R* gx, R* gp,
+                                                     const Cache& k)
+    {
+        R a[3], b[3];
+        rates_from(x[0], k, a, b);
         const R V = x[0], m = x[1], h = x[2], n = x[3];
+        const R dh = dh_of(k.E);
         R da[3], db[3];
-        da[0] = dpsi_em<R>((V + R(40)) * R(0.1), em_m) * R(0.1);
+        da[0] = dpsi_em<R>((V + R(40)) * R(0.1), k.dm, k.r * k.dn * dh) * R(0.1);
         db[0] = b[0] * R(-1.0 / 18.0);
         da[1] = a[1] * R(-0.05);
         db[1] = b[1] * (R(1) - b[1]) * R(0.1);
-        da[2] = dpsi_em<R>((V + R(55)) * R(0.1), em_n) * R(0.01);
+        da[2] = dpsi_em<R>((V + R(55)) * R(0.1), k.dn, k.r * k.dm * dh) * R(0.01);
         db[2] = b[2] * R(-0.0125);
         const R gNa = q[0], gK = q[1], gL = q[2], ENa = q[3], EK = q[4], EL = q[5], iC = q[7];
         const R m3h = m * m * m * h, n4 = n * n * n * n;
@@ -366,6 +409,30 @@ enum : int { kProposalGauss = 0, kProposalUniform = 1 };
         return FN<Toy1D<float>, float>(__VA_ARGS__);                                      \
     } while (0)
 
+// Forward stage evaluations that keep what the reverse pass can reuse: for a
+// model with kReuseRates, rhs_c / rhs_vjp_c and its Cache; otherwise an empty
+// record and the plain rhs / rhs_vjp.
+template <class Model, class = void> struct ModelCache {
+    struct type {};
+    template <class R>
+    static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F, type&) { Model::rhs(x, q, I, F); }
+    template <class R>
+    static __device__ __forceinline__ void vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp, const type&)
+    {
+        Model::rhs_vjp(x, q, I, w, gx, gp);
+    }
+};
+template <class Model> struct ModelCache<Model, typename std::enable_if<Model::kReuseRates>::type> {
+    using type = typename Model::Cache;
+    template <class R>
+    static __device__ __forceinline__ void rhs(const R* x, const R* q, R I, R* F, type& k) { Model::rhs_c(x, q, I, F, k); }
+    template <class R>
+    static __device__ __forceinline__ void vjp(const R* x, const R* q, R I, const R* w, R* gx, R* gp, const type& k)
+    {
+        Model::rhs_vjp_c(x, q, I, w, gx, gp, k);
+    }
+};
+
 // One classical RK4 step of size dt with the drive held at I:
 // f = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).
 template <class Model, class R>
@@ -397,16 +464,17 @@ __device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, Cot c
 {
     constexpr int D = Model::D;
     R k1[D], k2[D], k3[D], k4[D], x2[D], x3[D], x4[D];
-    Model::rhs(x, p, I, k1);
+    typename ModelCache<Model>::type c1, c2, c3, c4;
+    ModelCache<Model>::rhs(x, p, I, k1, c1);
 #pragma unroll
     for (int a = 0; a < D; ++a) x2[a] = x[a] + R(0.5) * dt * k1[a];
-    Model::rhs(x2, p, I, k2);
+    ModelCache<Model>::rhs(x2, p, I, k2, c2);
 #pragma unroll
     for (int a = 0; a < D; ++a) x3[a] = x[a] + R(0.5) * dt * k2[a];
-    Model::rhs(x3, p, I, k3);
+    ModelCache<Model>::rhs(x3, p, I, k3, c3);
 #pragma unroll
     for (int a = 0; a < D; ++a) x4[a] = x[a] + dt * k3[a];
-    Model::rhs(x4, p, I, k4);
+    ModelCache<Model>::rhs(x4, p, I, k4, c4);
     R f[D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -424,16 +492,16 @@ __device__ __forceinline__ void rk4_vjp(const R* x, const R* p, R I, R dt, Cot c
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = R(0);
-    Model::rhs_vjp(x4, p, I, b4, u, gp);
+    ModelCache<Model>::vjp(x4, p, I, b4, u, gp, c4);
 #pragma unroll
     for (int a = 0; a < D; ++a) { gx[a] += u[a]; b3[a] += dt * u[a]; u[a] = R(0); }
-    Model::rhs_vjp(x3, p, I, b3, u, gp);
+    ModelCache<Model>::vjp(x3, p, I, b3, u, gp, c3);
 #pragma unroll
     for (int a = 0; a < D; ++a) { gx[a] += u[a]; b2[a] += R(0.5) * dt * u[a]; u[a] = R(0); }
-    Model::rhs_vjp(x2, p, I, b2, u, gp);
+    ModelCache<Model>::vjp(x2, p, I, b2, u, gp, c2);
 #pragma unroll
     for (int a = 0; a < D; ++a) { gx[a] += u[a]; b1[a] += R(0.5) * dt * u[a]; u[a] = R(0); }
-    Model::rhs_vjp(x, p, I, b1, u, gp);
+    ModelCache<Model>::vjp(x, p, I, b1, u, gp, c1);
 #pragma unroll
     for (int a = 0; a < D; ++a) gx[a] += u[a];
 }

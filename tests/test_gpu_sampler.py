@@ -148,12 +148,16 @@ def test_T_ERR_boundary_rejects_bad_arguments():
     assert np.isfinite(A)
 
 
-def test_T_FAULT_bounded_barrier_wait_reports_timeout():
+@pytest.mark.parametrize("precision", ["fp64", "fp32mixed"])
+def test_T_FAULT_bounded_barrier_wait_reports_timeout(precision):
     """One CTA skips its barrier arrivals (a flag nothing else sets): the other
     CTAs' bounded waits expire, the launch returns, the status reads
-    PIMC_ERR_TIMEOUT, and the handle works again afterwards."""
+    PIMC_ERR_TIMEOUT, and the handle works again afterwards.  FP64 runs the
+    general form (grid barriers), FP32-mixed the resident form (counted
+    parameter-move sums and neighbour flags)."""
     prob = synth.hh_problem(2000, data_seed=0)
-    g = pimc.Sampler.from_problem(prob)
+    g = pimc.Sampler.from_problem(prob, precision=pimc.FP64 if precision == "fp64" else pimc.FP32_MIXED)
+    assert g.sweep_form() == ("general" if precision == "fp64" else "resident")
     grid, _ = g.launch_info()
     assert grid >= 2
     g.set_wait_limit(200_000_000)  # 0.2 s
