@@ -41,6 +41,27 @@ def test_gpu_grad_matches_oracle_reverse_mode(setup):
     np.testing.assert_allclose(gpg, gpo, rtol=1e-10)
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_gpu_grad_strided_tiles_matches_oracle(scheme):
+    """600 001 sites: more tiles than CTAs, so every CTA of the gather-form
+    gradient kernel strides over several tiles (both discretisations)."""
+    prob = synth.hh_problem(600000, data_seed=1)
+    prob.scheme = scheme
+    X = synth.random_path_near(prob, prob.X_true, 0.5 * prob.sig_x, seed=3)
+    g = pimc.Sampler.from_problem(prob)
+    g.set_path(X)
+    o = oracle.Chain(0, prob.M, prob.dt, prob.Rm, prob.Rf)
+    o.set_scheme(scheme)
+    o.set_data(prob.y, prob.I)
+    o.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+    o.set_path(X)
+    gXg, gpg = g.grad(0.7)
+    gXo, gpo = o.grad(0.7)
+    scale = np.abs(gXo).max(axis=1, keepdims=True)
+    assert np.max(np.abs(gXg - gXo) / scale) < 1e-11
+    np.testing.assert_allclose(gpg, gpo, rtol=1e-9)
+
+
 def test_gpu_grad_matches_central_differences(setup):
     prob, X, g = setup
     gX, gp = g.grad(1.0)
