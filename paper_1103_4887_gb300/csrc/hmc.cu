@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kBlock) hmc_begin_kernel(Ctx c, HmcScalars* hs
         hs->E = -log(u01d(wacc.x, wacc.y));
         hs->eps = eps_t;
         hs->oob = 0;
+        hs->accept = 0;  // set by the last leapfrog step
     }
 }
 

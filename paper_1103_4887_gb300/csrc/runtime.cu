@@ -807,6 +807,7 @@ int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv
         CK(h, cudaMemcpyAsync(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
         *n_accepted = (int64_t)(hs.n_acc - acc0);
+        return pimc_sync(h);  // sticky status of the handle (a timed-out wait of an earlier launch)
     }
     return PIMC_OK;
 }
@@ -945,6 +946,7 @@ int pimc_set_wait_limit(pimc_t h, int64_t ns)
 {
     if (!h || ns < 1000) return h ? fail(h, PIMC_ERR_ARG, "wait limit must be >= 1000 ns") : PIMC_ERR_ARG;
     h->wait_ns = ns;
+    h->ctx_version++;  // captured into the HMC graph
     return PIMC_OK;
 }
 
@@ -971,6 +973,7 @@ int pimc_debug_skip_arrive(pimc_t h, int cta)
 {
     if (!h) return PIMC_ERR_ARG;
     h->skip_cta = cta;
+    h->ctx_version++;  // captured into the HMC graph
     return PIMC_OK;
 }
 
