@@ -166,12 +166,13 @@ template <class R> struct HH {
     // The transcendental part of the rates at V: E, e^{-t/18}, the psi
     // denominators dm, dn (1 - e^{-u} of alpha_m, alpha_n) and the shared
     // reciprocal r = 1/(dm dn dh), dh = 1 + E^8 e^3.  The reverse pass of an
-    // RK4 step reuses the forward pass's (kReuseRates), in FP64 where each
-    // exponential and division is a long FP64 instruction sequence.
+    // RK4 step reuses the forward pass's (kReuseRates): in FP64 each
+    // exponential and division is a long FP64 instruction sequence, in FP32
+    // the reuse shortens the latency-bound adjoint's chain.
     struct Cache {
         R E, e18, dm, dn, r;
     };
-    static constexpr bool kReuseRates = sizeof(R) == sizeof(double);
+    static constexpr bool kReuseRates = true;
     static __device__ __forceinline__ R dh_of(R E)
     {
         const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
