@@ -38,7 +38,7 @@ SEED = 1
 REF_BUDGET_S = 120.0
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
 # the resident sweep kernel on this workload, cold cache
-RESIDENT_STEP_DRAM_BYTES = 7.857e6
+RESIDENT_STEP_DRAM_BYTES = 7.849e6
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations + stage combinations):
@@ -351,7 +351,7 @@ def run_mixed(args):
     from paper_1103_4887_gb300 import diagnostics, pimc, synth
     M = args.M
     prob = synth.hh_problem(M, data_seed=0, free="all")
-    out = {"M": M, "n_free": 7, "length_scale": scale}
+    out = {"M": M, "n_free": 7}
     st = torch.cuda.current_stream()
     # (1) Delta A on the same states and proposals
     X = synth.random_path_near(prob, prob.X_true, 0.5 * prob.sig_x, seed=11)
