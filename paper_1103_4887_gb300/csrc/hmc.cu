@@ -4,16 +4,14 @@
 // named among the methods that sample exp(-A)); this is that form.
 //
 // One trajectory is a fixed sequence of launches on the handle's stream:
-// begin (state -> FP64 positions Q_0, momenta P drawn, kinetic energy K0,
-// step jitter and accept uniform), then n_leap + 1 leapfrog kernels -- step
+// begin (state -> positions Q_0, momenta P drawn, kinetic energy K0, step
+// jitter and accept uniform), then n_leap + 1 leapfrog kernels -- step
 // k evaluates the gradient at Q_k and applies P -= c_k eps g (c = 1/2 at both
 // ends, 1 between) and Q_{k+1} = Q_k + eps invm P, with the action at Q_0 and
 // at Q_L and the final kinetic energy and accept test folded into the end
 // steps -- then commit (accepted Q_L -> state, f cache refreshed), statistics
 // and the counter tick.  The host captures it once in a CUDA graph and
 // replays the graph per trajectory; every decision stays on the device.
-#include <cstddef>
-
 #include "device.cuh"
 #include "internal.h"
 #include "reduce.cuh"
