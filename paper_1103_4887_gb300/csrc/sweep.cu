@@ -1187,19 +1187,50 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
     sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
 }
 
-// The parameter draws of the next n sweeps of a chain, one thread a (sweep,
-// parameter): out[2 (k NP + l)] = z, out[2 (k NP + l) + 1] = -log u for sweep
-// st->sweep + k.  The same values the sweep draws itself (param_draw).
+// The parameter draws of the next n sweeps of a chain: out[2 (k NP + l)] = z,
+// out[2 (k NP + l) + 1] = -log u for sweep st->sweep + k -- the same values
+// the sweep draws itself (param_draw).  Four lanes a (sweep, parameter) take
+// the three independent FP64 chains in parallel (FP64 issues slowly on this
+// part, so the draws' latency, ahead of every resident launch, is the longest
+// chain): the Box-Muller radius sqrt(-2 log u1), the cosine cos(2 pi u2) and
+// -log u of the accept uniform; z = radius * cosine as in the one-thread form.
+// Also zeroes the three rotating accumulator slots of the exact sums.
 template <int NP>
 __global__ void __launch_bounds__(256) param_draws_kernel(Ctx c, int64_t n, double* out)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * NP) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 12) ((unsigned long long*)c.partials)[t] = 0ull;
+    const int64_t idx = t >> 2;  // (sweep, parameter)
+    const int role = (int)(t & 3);
+    const bool valid = idx < n * NP;
     const int l = (int)(idx % NP);
-    double z = 0.0, elog = 0.0;
-    if ((c.st->free_mask >> l) & 1u) param_draw(c, c.st->sweep + idx / NP, l, z, elog);
-    out[2 * idx] = z;
-    out[2 * idx + 1] = elog;
+    const long long s = c.st->sweep + idx / NP;
+    const bool draw = valid && ((c.st->free_mask >> l) & 1u);
+    double v = 0.0;
+    if (draw) {
+        if (role < 2) {
+            const uint4 wz = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 0u);
+            if (c.proposal == kProposalUniform) {
+                v = role == 0 ? 2.0 * u01d(wz.x, wz.y) - 1.0 : 1.0;
+            } else if (role == 0) {
+                v = sqrt(-2.0 * log(u01d(wz.x, wz.y)));
+            } else {
+                double sn, cs;
+                sincospi(2.0 * u01d(wz.z, wz.w), &sn, &cs);
+                v = cs;
+            }
+        } else if (role == 2) {
+            const uint4 w = draw_block(c.seed, c.chain, (uint64_t)s, (uint32_t)l, kKindParam, 1u);
+            v = -log(u01d(w.x, w.y));
+        }
+    }
+    // lanes 4j..4j+3 of a warp hold one (sweep, parameter)
+    const double cosv = __shfl_down_sync(0xffffffffu, v, 1);
+    const double elog = __shfl_down_sync(0xffffffffu, v, 2);
+    if (valid && role == 0) {
+        out[2 * idx] = draw ? (c.proposal == kProposalUniform ? v : v * cosv) : 0.0;
+        out[2 * idx + 1] = draw ? elog : 0.0;
+    }
 }
 
 // Resident form (FP32-mixed): tiles of at most kSweepBlock - 32 sites, even
@@ -1264,14 +1295,16 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
     void* args[] = {(void*)&cc, (void*)&ns};
     const bool res = resident && resident_fits(prec_of<R>(), c.tile, grid) && c.pdraw && n_sweeps <= kDrawChunk;
     if (res && n_sweeps > 0) {
-        const int64_t nt = n_sweeps * Model::NP;
+        // the draws kernel also zeroes the accumulator slots of the exact sums
+        const int64_t nt = 4 * n_sweeps * Model::NP;
         param_draws_kernel<Model::NP><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(c, n_sweeps, const_cast<double*>(c.pdraw));
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    } else {
+        // the three accumulator slots of the exact parameter-move sums start at zero
+        const cudaError_t e = cudaMemsetAsync(c.partials, 0, 12 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
     }
-    // the three accumulator slots of the exact parameter-move sums start at zero
-    const cudaError_t e = cudaMemsetAsync(c.partials, 0, 12 * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
     const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, 0, s);
 }
