@@ -138,6 +138,174 @@ template <class R> __device__ __forceinline__ R dpsi_em(R u, R em, R inv_em)
     return (em - u * (R(1) - em)) * (inv_em * inv_em);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 lanes.  The FP32 HH field and RK4 map are written once over a lane type
+// T: float (one site) or float2 (two sites, on the packed f32x2 add, mul and
+// fma of sm_100 and later, one issue slot for both lanes).  Every operation is
+// an explicitly rounded IEEE operation, and no product feeds an addition:
+// the code generator may fuse a packed multiply into a following packed add
+// (it never fuses the scalar __fmul_rn), so every such pair is written as an
+// fma on both sides.  A site's bits are then the same evaluated alone or as
+// one lane of a pair.  The SFU operations (ex2, rcp) run per lane.
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+
+__device__ __forceinline__ float ladd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 ladd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float lsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float2 lsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float lmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 lmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float lfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 lfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// c - a b, rounded once
+__device__ __forceinline__ float lfnma(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+__device__ __forceinline__ float2 lfnma(float2 a, float2 b, float2 c)
+{
+    return __ffma2_rn(make_float2(-a.x, -a.y), b, c);
+}
+// 2^x and 1/x on the SFU (ex2.approx, rcp.approx), per lane
+__device__ __forceinline__ float lex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 lex2(float2 x) { return make_float2(lex2(x.x), lex2(x.y)); }
+__device__ __forceinline__ float lrcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 lrcp(float2 x) { return make_float2(lrcp(x.x), lrcp(x.y)); }
+// |u| < cut ? s : v, per lane
+__device__ __forceinline__ float lsel_small(float u, float cut, float s, float v) { return fabsf(u) < cut ? s : v; }
+__device__ __forceinline__ float2 lsel_small(float2 u, float cut, float2 s, float2 v)
+{
+    return make_float2(lsel_small(u.x, cut, s.x, v.x), lsel_small(u.y, cut, s.y, v.y));
+}
+
+// The transcendental part of the HH rates at V (see HH below): E = e^{-(V+65)/80},
+// e^{-(V+65)/18}, the psi denominators dm, dn and the reciprocal r = 1/(dm dn dh).
+template <class T> struct HHCache {
+    T E, e18, dm, dn, r;
+};
+
+// HH rates and field over FP32 lanes.  e^y is formed as 2^(y log2 e) on the
+// SFU, with log2 e folded into each argument's constant; psi(u) = u/(1 - e^{-u})
+// takes the series 1 + u/2 + u^2/12 below |u| < 1e-2 (a per-lane select).
+template <class T> struct HHLanes {
+    static constexpr double kLog2e = 1.4426950408889634;
+    static constexpr float kCut = 1e-2f;
+    static __device__ __forceinline__ T psi_series(T u)
+    {
+        return lfma(u, lfma(u, splat<T>(float(1.0 / 12.0)), splat<T>(0.5f)), splat<T>(1.0f));
+    }
+    // arguments of alpha_m and alpha_n: (V + 40)/10 and (V + 55)/10
+    static __device__ __forceinline__ T um_of(T V) { return lfma(V, splat<T>(0.1f), splat<T>(4.0f)); }
+    static __device__ __forceinline__ T un_of(T V) { return lfma(V, splat<T>(0.1f), splat<T>(5.5f)); }
+    // dh = 1 + E^8 e^3 (= 1 + e^{-(V+35)/10})
+    static __device__ __forceinline__ T dh_of(T E)
+    {
+        const T E2 = lmul(E, E), E4 = lmul(E2, E2), E8 = lmul(E4, E4);
+        return lfma(E8, splat<T>(20.085536923187668f), splat<T>(1.0f));
+    }
+    static __device__ __forceinline__ void cache_at(T V, HHCache<T>& k)
+    {
+        const T t = ladd(V, splat<T>(65.0f));
+        k.E = lex2(lmul(t, splat<T>(float(-kLog2e / 80.0))));
+        k.e18 = lex2(lmul(t, splat<T>(float(-kLog2e / 18.0))));
+        const T um = um_of(V), un = un_of(V);
+        const T one = splat<T>(1.0f);
+        k.dm = lsel_small(um, kCut, one, lsub(one, lex2(lmul(um, splat<T>(float(-kLog2e))))));
+        k.dn = lsel_small(un, kCut, one, lsub(one, lex2(lmul(un, splat<T>(float(-kLog2e))))));
+        k.r = lrcp(lmul(lmul(k.dm, k.dn), dh_of(k.E)));
+    }
+    // alpha (a) and beta (b) of the gates m, h, n from the cache
+    static __device__ __forceinline__ void rates_from(T V, const HHCache<T>& k, T a[3], T b[3])
+    {
+        const T um = um_of(V), un = un_of(V);
+        const T nm = lsel_small(um, kCut, psi_series(um), um);
+        const T nn = lsel_small(un, kCut, psi_series(un), un);
+        const T dh = dh_of(k.E);
+        const T E2 = lmul(k.E, k.E), E4 = lmul(E2, E2);
+        b[2] = lmul(splat<T>(0.125f), k.E);
+        a[1] = lmul(splat<T>(0.07f), E4);
+        b[0] = lmul(splat<T>(4.0f), k.e18);
+        a[0] = lmul(nm, lmul(lmul(k.dn, dh), k.r));
+        a[2] = lmul(lmul(splat<T>(0.1f), nn), lmul(lmul(k.dm, dh), k.r));
+        b[1] = lmul(lmul(k.dm, k.dn), k.r);
+    }
+    // F = (dV/dt, dm/dt, dh/dt, dn/dt); q = (gNa, gK, gL, ENa, EK, EL, C, 1/C).
+    // The same rates as rates_from, with each alpha + beta formed by an fma
+    // and the currents scaled by 1/C term by term, so that every value that
+    // reaches an addition is an fma result (see the lane rules above).
+    static __device__ __forceinline__ void rhs(const T* x, const T* q, T I, T* F, HHCache<T>& k)
+    {
+        const T V = x[0], m = x[1], h = x[2], n = x[3];
+        cache_at(V, k);
+        const T um = um_of(V), un = un_of(V);
+        const T nm = lsel_small(um, kCut, psi_series(um), um);
+        const T nn = lsel_small(un, kCut, psi_series(un), un);
+        const T dh = dh_of(k.E);
+        const T E2 = lmul(k.E, k.E), E4 = lmul(E2, E2);
+        const T a0 = lmul(nm, lmul(lmul(k.dn, dh), k.r));
+        const T a1 = lmul(splat<T>(0.07f), E4);
+        const T a2 = lmul(lmul(splat<T>(0.1f), nn), lmul(lmul(k.dm, dh), k.r));
+        // alpha (1 - s) - beta s = alpha - (alpha + beta) s; beta_m = 4 e18,
+        // beta_h = dm dn r, beta_n = E / 8
+        F[1] = lfnma(lfma(splat<T>(4.0f), k.e18, a0), m, a0);
+        F[2] = lfnma(lfma(lmul(k.dm, k.dn), k.r, a1), h, a1);
+        F[3] = lfnma(lfma(splat<T>(0.125f), k.E, a2), n, a2);
+        const T iC = q[7];
+        const T m3h = lmul(lmul(lmul(m, m), m), h);
+        const T n2 = lmul(n, n), n4 = lmul(n2, n2);
+        T acc = lfnma(lmul(lmul(q[0], iC), m3h), lsub(V, q[3]), lmul(I, iC));
+        acc = lfnma(lmul(lmul(q[1], iC), n4), lsub(V, q[4]), acc);
+        F[0] = lfnma(lmul(q[2], iC), lsub(V, q[5]), acc);
+    }
+};
+
+// One classical RK4 step of the HH field over FP32 lanes (drive held at I):
+// f = x + dt/6 (k1 + 2 k2 + 2 k3 + k4); hdt = dt/2 and sdt = dt/6 as formed
+// by the caller.
+template <class T>
+__device__ __forceinline__ void hh_rk4_lanes(const T* x, const T* q, T I, T dt, T hdt, T sdt, T* f)
+{
+    T k[4], xs[4], acc[4];
+    HHCache<T> c;
+    HHLanes<T>::rhs(x, q, I, k, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { acc[a] = k[a]; xs[a] = lfma(hdt, k[a], x[a]); }
+    HHLanes<T>::rhs(xs, q, I, k, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { acc[a] = lfma(splat<T>(2.0f), k[a], acc[a]); xs[a] = lfma(hdt, k[a], x[a]); }
+    HHLanes<T>::rhs(xs, q, I, k, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) { acc[a] = lfma(splat<T>(2.0f), k[a], acc[a]); xs[a] = lfma(dt, k[a], x[a]); }
+    HHLanes<T>::rhs(xs, q, I, k, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) f[a] = lfma(sdt, ladd(acc[a], k[a]), x[a]);
+}
+
+// RK4 change of the model-error term of one site over FP32 lanes:
+// beta sum_a 1/2 Rf_a (d'_a - d_a)(d'_a + d_a), d' = x_{n+1} - f', d = x_{n+1} - f.
+template <class T, int D>
+__device__ __forceinline__ T rk4_term_lanes(T beta, const float* Rf, const T* xn1, const T* fnew, const T* fold)
+{
+    T t = splat<T>(0.0f);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const T dp = lsub(xn1[a], fnew[a]), d = lsub(xn1[a], fold[a]);
+        const T w = lmul(lmul(splat<T>(0.5f * Rf[a]), lsub(dp, d)), ladd(dp, d));
+        t = lfma(beta, w, t);
+    }
+    return t;
+}
+
 // Hodgkin-Huxley (1952) in the modern convention, conductance form:
 //   C dV/dt = I - gNa m^3 h (V - ENa) - gK n^4 (V - EK) - gL (V - EL)
 //   da/dt = alpha_a(V)(1 - a) - beta_a(V) a          (Sec. 5.1, Eq. (dadt) structure)
@@ -169,17 +337,25 @@ template <class R> struct HH {
     // RK4 step reuses the forward pass's (kReuseRates): in FP64 each
     // exponential and division is a long FP64 instruction sequence, in FP32
     // the reuse shortens the latency-bound adjoint's chain.
-    struct Cache {
-        R E, e18, dm, dn, r;
-    };
+    // FP32 (the FP32-mixed form): the same rates, evaluated by HHLanes<float>.
+    using Cache = HHCache<R>;
     static constexpr bool kReuseRates = true;
+    static constexpr bool kLanes = std::is_same<R, float>::value;
     static __device__ __forceinline__ R dh_of(R E)
     {
-        const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
-        return R(1) + E8 * R(20.085536923187668);  // e^3
+        if constexpr (kLanes) {
+            return HHLanes<float>::dh_of(E);
+        } else {
+            const R E2 = E * E, E4 = E2 * E2, E8 = E4 * E4;
+            return R(1) + E8 * R(20.085536923187668);  // e^3
+        }
     }
     static __device__ __forceinline__ void cache_at(R V, Cache& k)
     {
+        if constexpr (kLanes) {
+            HHLanes<float>::cache_at(V, k);
+            return;
+        }
         const R t = V + R(65);
         k.E = Num<R>::ex(t * R(-0.0125));
         k.e18 = Num<R>::ex(t * R(-1.0 / 18.0));
@@ -190,6 +366,10 @@ template <class R> struct HH {
     }
     static __device__ __forceinline__ void rates_from(R V, const Cache& k, R a[3], R b[3])
     {
+        if constexpr (kLanes) {
+            HHLanes<float>::rates_from(V, k, a, b);
+            return;
+        }
         const R E2 = k.E * k.E, E4 = E2 * E2;
         b[2] = R(0.125) * k.E;
         a[1] = R(0.07) * E4;
@@ -208,6 +388,10 @@ template <class R> struct HH {
     // rhs, keeping the rates' transcendental part in k
     static __device__ __forceinline__ void rhs_c(const R* x, const R* q, R I, R* F, Cache& k)
     {
+        if constexpr (kLanes) {
+            HHLanes<float>::rhs(x, q, I, F, k);
+            return;
+        }
         R a[3], b[3];
         cache_at(x[0], k);
         rates_from(x[0], k, a, b);
@@ -439,6 +623,11 @@ template <class Model> struct ModelCache<Model, typename std::enable_if<Model::k
 template <class Model, class R>
 __device__ __forceinline__ void rk4_map(const R* x, const R* p, R I, R dt, R* f)
 {
+    if constexpr (std::is_same<Model, HH<float>>::value) {
+        // FP32 HH: the lane form, bit for bit what a paired evaluation gives
+        hh_rk4_lanes<float>(x, p, I, dt, __fmul_rn(0.5f, dt), __fdiv_rn(dt, 6.0f), f);
+        return;
+    }
     constexpr int D = Model::D;
     R k[D], xs[D], acc[D];
     Model::rhs(x, p, I, k);

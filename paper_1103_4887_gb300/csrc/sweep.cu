@@ -341,13 +341,16 @@ __device__ __forceinline__ R param_term(const Ctx& c, const Coef<R>& k, int64_t 
         fc[a] = Fc[a * c.ldf + n];
     }
     rk4_map<Model, R>(x, pq, ((const R*)c.I)[n], k.dt, fp);
-    R t = R(0);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        Fn[a * c.ldf + n] = fp[a];
-        t += beta * sqdiff<R>(k.Rf[a], xn1[a] - fp[a], xn1[a] - fc[a]);
+    for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = fp[a];
+    if constexpr (std::is_same<R, float>::value) {
+        return rk4_term_lanes<float, D>(beta, k.Rf, xn1, fp, fc);
+    } else {
+        R t = R(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) t += beta * sqdiff<R>(k.Rf[a], xn1[a] - fp[a], xn1[a] - fc[a]);
+        return t;
     }
-    return t;
 }
 
 // Trapezoid scheme, first pass: F(x_n, p') of site n into the inactive cache.
@@ -726,6 +729,45 @@ __device__ __forceinline__ void store_chain_state(const Ctx& c, SweepShared<R, N
     __syncthreads();
 }
 
+// RK4 scheme, FP32 HH: the sites [n0, nend) of a parameter move two at a time,
+// (n, n + 1) with n - n0 even, on the packed f32x2 lane form -- per site the
+// same bits as param_term.  n0 is even (tiles have even length), so the pair
+// loads and stores are 8-byte aligned; an unpaired last site is lane x alone
+// (lane y then reads x_{n+1}, f_{n+1}, I_{n+1}, inside the rows, and is
+// dropped).
+template <int NT>
+__device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<float>& k, int64_t n0, int64_t nend,
+                                                   const float* pq, float beta, const float* Fc, float* Fn,
+                                                   Fix3& part)
+{
+    const float* X = (const float*)c.X;
+    const float* I = (const float*)c.I;
+    float2 q2[kMaxP];
+#pragma unroll
+    for (int j = 0; j < kMaxP; ++j) q2[j] = splat<float2>(pq[j]);
+    const float2 dt2 = splat<float2>(k.dt), beta2 = splat<float2>(beta);
+    const float2 hdt2 = splat<float2>(__fmul_rn(0.5f, k.dt)), sdt2 = splat<float2>(__fdiv_rn(k.dt, 6.0f));
+    for (int64_t n = n0 + 2 * (int64_t)threadIdx.x; n < nend; n += 2 * NT) {
+        const bool two = n + 1 < nend;
+        float2 x[4], xn1[4], fc[4], fp[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            x[a] = *(const float2*)(X + a * c.ldx + n);
+            xn1[a] = make_float2(x[a].y, two ? X[a * c.ldx + n + 2] : 0.0f);
+            fc[a] = *(const float2*)(Fc + a * c.ldf + n);
+        }
+        hh_rk4_lanes<float2>(x, q2, *(const float2*)(I + n), dt2, hdt2, sdt2, fp);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (two) *(float2*)(Fn + a * c.ldf + n) = fp[a];
+            else Fn[a * c.ldf + n] = fp[a].x;
+        }
+        const float2 t = rk4_term_lanes<float2, 4>(beta2, k.Rf, xn1, fp, fc);
+        fix_add(part, t.x);
+        if (two) fix_add(part, t.y);
+    }
+}
+
 // ---- general form -----------------------------------------------------------
 
 // n_sweeps checkerboard sweeps of one chain over the sites [n0, n1) this CTA
@@ -778,7 +820,11 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             fix_zero(part);
             const int64_t nend = min(n1, M);
             if (c.scheme == kSchemeRK4) {
-                for (int64_t n = n0 + tid; n < nend; n += NT) fix_add(part, param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn));
+                if constexpr (std::is_same<Model, HH<float>>::value)
+                    param_terms_paired<NT>(c, kc, n0, nend, pq, beta, Fc, Fn, part);
+                else
+                    for (int64_t n = n0 + tid; n < nend; n += NT)
+                        fix_add(part, param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn));
             } else {
                 // trapezoid: F(x_n, p') of the tile (and of the next tile's
                 // first site, recomputed here), then the residual changes
@@ -862,6 +908,9 @@ template <class R, int D>
 __device__ __forceinline__ R move_term(const Ctx& c, const Coef<R>& k, bool trap, const R* x, const R* xn,
                                        const R* g, const R* gn, const R* f, const R* fn, R beta)
 {
+    if constexpr (std::is_same<R, float>::value) {
+        if (!trap) return rk4_term_lanes<float, D>(beta, k.Rf, xn, f, g);
+    }
     R t = R(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -1074,12 +1123,46 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                         }
                     } else if (own && l2 >= 0) {
                         // speculation: move l2's values for both outcomes of
-                        // move l, one map instance evaluated twice (two inlined
-                        // copies would share subexpressions, and the compiler
-                        // would fuse multiply-adds differently from the
-                        // general form's single map)
+                        // move l.  FP32 HH under the RK4 scheme: both maps as
+                        // the two lanes of one packed evaluation (lane x:
+                        // reject, lane y: accept), each lane bit for bit the
+                        // single map.  Otherwise one map instance evaluated
+                        // twice (two inlined copies would share
+                        // subexpressions, and the compiler would fuse
+                        // multiply-adds differently from the general form's
+                        // single map).
+                        bool spec_done = false;
+                        if constexpr (std::is_same<Model, HH<float>>::value) {
+                            if (!trap) {
+                                spec_done = true;
+                                if (has_next) {
+                                    R qR[kMaxP], qA[kMaxP];
+#pragma unroll
+                                    for (int j = 0; j < kMaxP; ++j) qR[j] = pr[j];
+                                    apply_move<R, NT>(qR, sh, l2);
+#pragma unroll
+                                    for (int j = 0; j < kMaxP; ++j) qA[j] = qR[j];
+                                    apply_move<R, NT>(qA, sh, l);
+                                    float2 q2[kMaxP], x2[D], f2[D];
+#pragma unroll
+                                    for (int j = 0; j < kMaxP; ++j) q2[j] = make_float2(qR[j], qA[j]);
+#pragma unroll
+                                    for (int a = 0; a < D; ++a) x2[a] = splat<float2>(xr[a]);
+                                    hh_rk4_lanes<float2>(x2, q2, splat<float2>(drive), splat<float2>(kc.dt),
+                                                         splat<float2>(__fmul_rn(0.5f, kc.dt)),
+                                                         splat<float2>(__fdiv_rn(kc.dt, 6.0f)), f2);
+#pragma unroll
+                                    for (int a = 0; a < D; ++a) {
+                                        fR[a] = f2[a].x;
+                                        fA[a] = f2[a].y;
+                                    }
+                                }
+#pragma unroll
+                                for (int a = 0; a < D; ++a) fnA[a] = fnR[a] = R(0);
+                            }
+                        }
 #pragma unroll 1
-                        for (int o = 0; o < 2; ++o) {
+                        for (int o = 0; o < (spec_done ? 0 : 2); ++o) {
                             R q[kMaxP], f2[D], fn2[D];
 #pragma unroll
                             for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
