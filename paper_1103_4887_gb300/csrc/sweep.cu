@@ -496,17 +496,47 @@ __device__ __forceinline__ bool fix_less(Fix3 s, double e)
     return s.c[0] < t.c[0];
 }
 
+// Warp sum of Fix3 values, valid in every lane.  Each lane's value is
+// normalised (c0, c1 in [0, 2^42)) and cut into 21-bit pieces -- the top
+// chunk's upper piece signed -- whose 32-lane sums fit 32-bit integers, so the
+// warp adds them with seven independent redux.sync reductions instead of
+// five dependent rounds of 64-bit shuffles.  A top chunk of 2^41 or more
+// (terms near the 2^62 limit) sends the warp to the shuffle rounds.
+__device__ __forceinline__ Fix3 fix_warp_sum(Fix3 f)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    fix_normalize(f);
+    const long long lim = 1ll << 41;
+    if (__any_sync(kAll, f.c[2] >= lim || f.c[2] < -lim)) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) f.c[j] += __shfl_xor_sync(kAll, f.c[j], off);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f.flags |= __shfl_xor_sync(kAll, f.flags, off);
+        return f;
+    }
+    const unsigned m21 = (1u << 21) - 1u;
+    const unsigned s0 = __reduce_add_sync(kAll, (unsigned)f.c[0] & m21);
+    const unsigned s1 = __reduce_add_sync(kAll, (unsigned)(f.c[0] >> 21));
+    const unsigned s2 = __reduce_add_sync(kAll, (unsigned)f.c[1] & m21);
+    const unsigned s3 = __reduce_add_sync(kAll, (unsigned)(f.c[1] >> 21));
+    const unsigned s4 = __reduce_add_sync(kAll, (unsigned)f.c[2] & m21);
+    const int s5 = __reduce_add_sync(kAll, (int)(f.c[2] >> 21));
+    Fix3 r;
+    r.c[0] = (long long)s0 + (long long)s1 * (1ll << 21);
+    r.c[1] = (long long)s2 + (long long)s3 * (1ll << 21);
+    r.c[2] = (long long)s4 + (long long)s5 * (1ll << 21);
+    r.flags = __reduce_or_sync(kAll, (unsigned)f.flags);
+    return r;
+}
+
 // CTA sum of every thread's Fix3 (one CTA barrier inside), carries
 // normalised; valid in thread 0.
 template <int NT>
 __device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
 {
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) f.c[j] += __shfl_xor_sync(0xffffffffu, f.c[j], off);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) f.flags |= __shfl_xor_sync(0xffffffffu, f.flags, off);
+    f = fix_warp_sum(f);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) wfix[w] = f;
     __syncthreads();
@@ -514,12 +544,7 @@ __device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
     fix_zero(t);
     if (threadIdx.x < 32) {
         if (lane < NT / 32) t = wfix[lane];
-#pragma unroll
-        for (int off = NT / 64; off > 0; off >>= 1) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) t.c[j] += __shfl_xor_sync(0xffffffffu, t.c[j], off);
-            t.flags |= __shfl_xor_sync(0xffffffffu, t.flags, off);
-        }
+        t = fix_warp_sum(t);
         fix_normalize(t);
     }
     return t;
