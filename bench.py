@@ -38,15 +38,17 @@ SEED = 1
 REF_BUDGET_S = 120.0
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
 # the resident sweep kernel on this workload, cold cache
-RESIDENT_STEP_DRAM_BYTES = 7.849e6
+RESIDENT_STEP_DRAM_BYTES = 7.844e6
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
-# form, counted from the formula (4 field evaluations + stage combinations):
-# FP32 instructions and SFU (MUFU) operations.
-FP32_OPS_PER_MAP = 232
-MUFU_OPS_PER_MAP = 36
+# form, counted from the formula (4 field evaluations of 50 FP32 operations
+# -- 16 of them fmas -- and 5 SFU operations: exponentials of -(V+65)/80,
+# -(V+65)/18 and the two psi arguments, one shared reciprocal; 28 stage
+# combinations, 24 of them fmas): FP32 instructions and SFU (MUFU) operations.
+FP32_OPS_PER_MAP = 228
+MUFU_OPS_PER_MAP = 20
 # FP32 floating-point operations per map (an FMA counted as 2).
-FLOP_PER_MAP = 300
+FLOP_PER_MAP = 316
 
 
 def maps_per_sweep(M, n_free):
