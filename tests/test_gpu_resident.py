@@ -3,8 +3,11 @@
 The resident form (one site a thread for the whole launch, flags between
 neighbouring CTAs, speculative parameter maps) and the general form (threads
 striding over the tile, grid barriers) evaluate the same per-site terms and
-sum the parameter-move partials in the same order, so on the same tiles every
-state, parameter, statistic and counter is identical."""
+sum the parameter-move partials exactly, so on the same tiles every state,
+parameter, statistic and counter is identical.  The FP32 HH map runs one site
+alone or two as the lanes of a packed map (general form: sites n, n + 1;
+resident form: a site's two speculative outcomes); the cached values that
+the residual statistics read expose any bit of difference between the two."""
 import numpy as np
 import pytest
 
@@ -40,12 +43,16 @@ def _same(a, b):
     assert a.sweep_counter() == b.sweep_counter()
 
 
-@pytest.mark.parametrize("case", ["hh_M1000", "hh_M237_grid3", "hh_M150_grid1", "hh_M1_grid1", "paper_M400",
-                                  "hh_trap_M600", "lg_M300", "toy_M90"])
+@pytest.mark.parametrize("case", ["hh_M1000", "hh_M1000_one_free", "hh_M237_grid3", "hh_M150_grid1", "hh_M1_grid1",
+                                  "paper_M400", "hh_trap_M600", "lg_M300", "toy_M90"])
 def test_resident_and_general_forms_agree_bitwise(case):
     grid = 0
     if case == "hh_M1000":
         prob = synth.hh_problem(1000, data_seed=3, free="all")
+    elif case == "hh_M1000_one_free":
+        # one parameter: the resident form evaluates every move's map one site
+        # at a time, the general form two sites a thread on the packed map
+        prob = synth.hh_problem(1000, data_seed=3, free=("gNa",))
     elif case == "hh_M237_grid3":
         prob, grid = synth.hh_problem(237, data_seed=5, free="all"), 3
     elif case == "hh_M150_grid1":

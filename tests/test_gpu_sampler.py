@@ -129,6 +129,14 @@ def test_T_ERR_boundary_rejects_bad_arguments():
         g.set_data(y, prob.I)
     assert e.value.code == pimc.ERR_ARG
     g.set_data(prob.y, prob.I)
+    # streaming data: non-finite values anywhere (also in the last, unrolled-off
+    # entries of the check) are rejected before anything is enqueued
+    for which, idx, val in (("y", prob.M, np.inf), ("I", prob.M - 1, -np.inf), ("I", 2, np.nan)):
+        yy, II = prob.y.copy(), prob.I.copy()
+        (yy if which == "y" else II)[idx] = val
+        with pytest.raises(pimc.PimcError) as e:
+            g.load_data(yy.ctypes.data, II.ctypes.data)
+        assert e.value.code == pimc.ERR_ARG
     bad = prob.p_init.copy()
     bad[0] = prob.hi[0] + 1.0
     with pytest.raises(pimc.PimcError) as e:
