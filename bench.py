@@ -34,6 +34,10 @@ METRIC = "HH Metropolis site-updates/s (M=32768, 7 free params, checkerboard swe
 UNIT = "site-updates/s"
 M_DEFAULT = 32768
 NSKIP = 10
+# The paper's own speedup (Sec. 5, Fig. speedup): other hardware, its FP32
+# tanh-model workload, against a different CPU code; context, not a target.
+PAPER_SPEEDUP_CONTEXT = ("T_CPU/T_GPU up to about 300 (GTX 470, 448 cores) and 200 (GTX 460) against one "
+                         "Intel Core i3 core, FP32, M = 100..40000, 1e5 sweeps")
 SEED = 1
 REF_BUDGET_S = 120.0
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
@@ -270,6 +274,7 @@ def run_sweep_M(args):
         if "s_per_sweep" in row["oracle_allcores"]:
             row["speedup_fp32_vs_oracle_allcores"] = (row["oracle_allcores"]["s_per_sweep"]
                                                       / (row["fp32mixed"]["ms_per_sweep"] * 1e-3))
+        row["paper_speedup_context"] = PAPER_SPEEDUP_CONTEXT
         print(json.dumps(row), flush=True)
 
 
