@@ -5,9 +5,12 @@
 //
 // A parameter move (Sec. 4.3) needs the whole path: every CTA evaluates the
 // map at the proposed p for its sites into the inactive half of the
-// double-buffered cache and a partial change of action; after one grid
-// barrier every CTA sums all partials in the same fixed order (FP64) and takes
-// the same accept decision, so no second launch or broadcast is needed.
+// double-buffered cache and a partial change of action, summed exactly (integer
+// chunks, see "exact sums" below); after one grid barrier every CTA reads the
+// same total and takes the same accept decision, so no second launch or
+// broadcast is needed.  In FP32 the HH map of a parameter move runs on packed
+// f32x2 arithmetic: two adjacent sites a thread in the general form, the two
+// speculative outcomes of a site in the resident form.
 //
 // Two forms of the site phases:
 //  * resident (tiles of at most NT - 32 sites): thread 32 + i owns site
