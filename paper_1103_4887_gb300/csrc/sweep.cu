@@ -1137,6 +1137,9 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     todo &= todo - 1u;
                     const int l2 = todo ? __ffs(todo) - 1 : -1;
                     R fA[D], fnA[D], fR[D], fnR[D];
+                    Fix3 tA, tR;  // move l2's term of this site for each outcome of move l
+                    fix_zero(tA);
+                    fix_zero(tR);
                     const unsigned slot = sh.nred % 3u;
                     const Fix3 cta = fix_cta_sum<NT>(mine, sh.wfix);  // exact CTA sum (a CTA barrier inside)
                     if (tid < 32) {
@@ -1208,6 +1211,12 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                                 }
                             }
                         }
+                        // and move l2's term for each outcome: accepting l
+                        // makes move l's values (f, fn) this site's cache
+                        if (has_next) {
+                            fix_add(tA, move_term<R, D>(c, kc, trap, xr, xn, f, fn, fA, fnA, beta));
+                            fix_add(tR, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, fR, fnR, beta));
+                        }
                     }
                     __syncthreads();
                     if (sh.abort) goto done;
@@ -1230,7 +1239,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                             f[a] = acc ? fA[a] : fR[a];
                             fn[a] = acc ? fnA[a] : fnR[a];
                         }
-                        if (has_next) fix_add(mine, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta));
+                        mine = acc ? tA : tR;
                         if (cached) {
                             R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
