@@ -56,6 +56,8 @@ template <class R, int NT> struct SweepShared {
     R gs[kMaxD][NT];                // resident form: cached value of site n0 + i at [a][i]
     Fix3 wfix[NT / 32];             // warp sums of a parameter move's exact CTA sum
     Fix3 cta_fix;                   // CTA sum of a parameter move (CTA-local chains)
+    Fix3 wspec[2][NT / 32];         // resident form: site warps' sums of the next move's terms (accept, reject)
+    Fix3 cta_spec[2][2];            // resident form: [buffer][accept, reject] CTA sums of the next move's terms
     unsigned long long ep0;         // resident form: epoch base of the neighbour flags
     unsigned bar_phase;             // top bit of the grid-barrier word before the next barrier
     int abort;
@@ -1133,6 +1135,11 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                         for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
                     }
                 }
+                // from the second move on, the CTA sums of the move's terms for
+                // both outcomes of the decision before were formed during that
+                // decision's barrier (buffer spec_buf)
+                bool spec_sums = false;
+                int spec_buf = 0;
                 while (true) {
                     todo &= todo - 1u;
                     const int l2 = todo ? __ffs(todo) - 1 : -1;
@@ -1141,7 +1148,14 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     fix_zero(tA);
                     fix_zero(tR);
                     const unsigned slot = sh.nred % 3u;
-                    const Fix3 cta = fix_cta_sum<NT>(mine, sh.wfix);  // exact CTA sum (a CTA barrier inside)
+                    Fix3 cta;
+                    if (spec_sums) {
+                        fix_zero(cta);
+                        if (tid == 0) cta = sh.cta_spec[spec_buf][sh.last_acc ? 0 : 1];
+                        spec_buf ^= 1;
+                    } else {
+                        cta = fix_cta_sum<NT>(mine, sh.wfix);  // exact CTA sum (a CTA barrier inside)
+                    }
                     if (tid < 32) {
                         // thread 0: publish, grid barrier, total, decide
                         if (lane == 0) {
@@ -1152,70 +1166,99 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                                 sync.recycle(c, slot);
                             }
                         }
-                    } else if (own && l2 >= 0) {
-                        // speculation: move l2's values for both outcomes of
-                        // move l.  FP32 HH under the RK4 scheme: both maps as
-                        // the two lanes of one packed evaluation (lane x:
-                        // reject, lane y: accept), each lane bit for bit the
-                        // single map.  Otherwise one map instance evaluated
-                        // twice (two inlined copies would share
-                        // subexpressions, and the compiler would fuse
-                        // multiply-adds differently from the general form's
-                        // single map).
-                        bool spec_done = false;
-                        if constexpr (std::is_same<Model, HH<float>>::value) {
-                            if (!trap) {
-                                spec_done = true;
-                                if (has_next) {
-                                    R qR[kMaxP], qA[kMaxP];
+                    } else if (l2 >= 0) {
+                        if (own) {
+                            // speculation: move l2's values for both outcomes of
+                            // move l.  FP32 HH under the RK4 scheme: both maps as
+                            // the two lanes of one packed evaluation (lane x:
+                            // reject, lane y: accept), each lane bit for bit the
+                            // single map.  Otherwise one map instance evaluated
+                            // twice (two inlined copies would share
+                            // subexpressions, and the compiler would fuse
+                            // multiply-adds differently from the general form's
+                            // single map).
+                            bool spec_done = false;
+                            if constexpr (std::is_same<Model, HH<float>>::value) {
+                                if (!trap) {
+                                    spec_done = true;
+                                    if (has_next) {
+                                        R qR[kMaxP], qA[kMaxP];
 #pragma unroll
-                                    for (int j = 0; j < kMaxP; ++j) qR[j] = pr[j];
-                                    apply_move<R, NT>(qR, sh, l2);
+                                        for (int j = 0; j < kMaxP; ++j) qR[j] = pr[j];
+                                        apply_move<R, NT>(qR, sh, l2);
 #pragma unroll
-                                    for (int j = 0; j < kMaxP; ++j) qA[j] = qR[j];
-                                    apply_move<R, NT>(qA, sh, l);
-                                    float2 q2[kMaxP], x2[D], f2[D];
+                                        for (int j = 0; j < kMaxP; ++j) qA[j] = qR[j];
+                                        apply_move<R, NT>(qA, sh, l);
+                                        float2 q2[kMaxP], x2[D], f2[D];
 #pragma unroll
-                                    for (int j = 0; j < kMaxP; ++j) q2[j] = make_float2(qR[j], qA[j]);
+                                        for (int j = 0; j < kMaxP; ++j) q2[j] = make_float2(qR[j], qA[j]);
 #pragma unroll
-                                    for (int a = 0; a < D; ++a) x2[a] = splat<float2>(xr[a]);
-                                    hh_rk4_lanes<float2>(x2, q2, splat<float2>(drive), splat<float2>(kc.dt),
-                                                         splat<float2>(__fmul_rn(0.5f, kc.dt)),
-                                                         splat<float2>(__fdiv_rn(kc.dt, 6.0f)), f2);
+                                        for (int a = 0; a < D; ++a) x2[a] = splat<float2>(xr[a]);
+                                        hh_rk4_lanes<float2>(x2, q2, splat<float2>(drive), splat<float2>(kc.dt),
+                                                             splat<float2>(__fmul_rn(0.5f, kc.dt)),
+                                                             splat<float2>(__fdiv_rn(kc.dt, 6.0f)), f2);
 #pragma unroll
-                                    for (int a = 0; a < D; ++a) {
-                                        fR[a] = f2[a].x;
-                                        fA[a] = f2[a].y;
+                                        for (int a = 0; a < D; ++a) {
+                                            fR[a] = f2[a].x;
+                                            fA[a] = f2[a].y;
+                                        }
+                                    }
+#pragma unroll
+                                    for (int a = 0; a < D; ++a) fnA[a] = fnR[a] = R(0);
+                                }
+                            }
+#pragma unroll 1
+                            for (int o = 0; o < (spec_done ? 0 : 2); ++o) {
+                                R q[kMaxP], f2[D], fn2[D];
+#pragma unroll
+                                for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
+                                apply_move<R, NT>(q, sh, l2);
+                                if (o == 1) apply_move<R, NT>(q, sh, l);
+                                move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f2, fn2);
+#pragma unroll
+                                for (int a = 0; a < D; ++a) {
+                                    if (o == 1) {
+                                        fA[a] = f2[a];
+                                        fnA[a] = fn2[a];
+                                    } else {
+                                        fR[a] = f2[a];
+                                        fnR[a] = fn2[a];
                                     }
                                 }
-#pragma unroll
-                                for (int a = 0; a < D; ++a) fnA[a] = fnR[a] = R(0);
+                            }
+                            // and move l2's term for each outcome: accepting l
+                            // makes move l's values (f, fn) this site's cache
+                            if (has_next) {
+                                fix_add(tA, move_term<R, D>(c, kc, trap, xr, xn, f, fn, fA, fnA, beta));
+                                fix_add(tR, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, fR, fnR, beta));
                             }
                         }
-#pragma unroll 1
-                        for (int o = 0; o < (spec_done ? 0 : 2); ++o) {
-                            R q[kMaxP], f2[D], fn2[D];
-#pragma unroll
-                            for (int j = 0; j < kMaxP; ++j) q[j] = pr[j];
-                            apply_move<R, NT>(q, sh, l2);
-                            if (o == 1) apply_move<R, NT>(q, sh, l);
-                            move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f2, fn2);
-#pragma unroll
-                            for (int a = 0; a < D; ++a) {
-                                if (o == 1) {
-                                    fA[a] = f2[a];
-                                    fnA[a] = fn2[a];
-                                } else {
-                                    fR[a] = f2[a];
-                                    fnR[a] = fn2[a];
-                                }
-                            }
+                        // CTA sums of those terms for both outcomes, by the site
+                        // warps alone (named barrier 1; warp 0 holds no site
+                        // and is in the grid barrier) -- exact, so the same
+                        // total as the sum after the decision
+                        const Fix3 wA = fix_warp_sum(tA), wR = fix_warp_sum(tR);
+                        if (lane == 0) {
+                            sh.wspec[0][tid >> 5] = wA;
+                            sh.wspec[1][tid >> 5] = wR;
                         }
-                        // and move l2's term for each outcome: accepting l
-                        // makes move l's values (f, fn) this site's cache
-                        if (has_next) {
-                            fix_add(tA, move_term<R, D>(c, kc, trap, xr, xn, f, fn, fA, fnA, beta));
-                            fix_add(tR, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, fR, fnR, beta));
+                        asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
+                        if (tid < 64) {
+                            Fix3 a, r;
+                            fix_zero(a);
+                            fix_zero(r);
+                            if (lane < NT / 32 - 1) {
+                                a = sh.wspec[0][lane + 1];
+                                r = sh.wspec[1][lane + 1];
+                            }
+                            a = fix_warp_sum(a);
+                            r = fix_warp_sum(r);
+                            fix_normalize(a);
+                            fix_normalize(r);
+                            if (lane == 0) {
+                                sh.cta_spec[spec_buf][0] = a;
+                                sh.cta_spec[spec_buf][1] = r;
+                            }
                         }
                     }
                     __syncthreads();
@@ -1232,14 +1275,13 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     }
                     if (l2 < 0) break;
                     l = l2;
-                    fix_zero(mine);
+                    spec_sums = true;
                     if (own) {
 #pragma unroll
                         for (int a = 0; a < D; ++a) {
                             f[a] = acc ? fA[a] : fR[a];
                             fn[a] = acc ? fnA[a] : fnR[a];
                         }
-                        mine = acc ? tA : tR;
                         if (cached) {
                             R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
