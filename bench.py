@@ -42,7 +42,7 @@ SEED = 1
 REF_BUDGET_S = 120.0
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
 # the resident sweep kernel on this workload, cold cache
-RESIDENT_STEP_DRAM_BYTES = 7.844e6
+RESIDENT_STEP_DRAM_BYTES = 7.856e6
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations of 50 FP32 operations
