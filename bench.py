@@ -42,7 +42,7 @@ SEED = 1
 REF_BUDGET_S = 120.0
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
 # the resident sweep kernel on this workload, cold cache
-RESIDENT_STEP_DRAM_BYTES = 7.856e6
+RESIDENT_STEP_DRAM_BYTES = 7.861e6
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations of 50 FP32 operations
@@ -731,7 +731,9 @@ def main():
                            "precision": args.precision, "sweeps_per_step": NSKIP, "n_skip": NSKIP,
                            "l2": "flushed (256 MiB write) before every timed step",
                            "grid_block": grid_block, "form": form},
-                "gpu_launches": args.steps,
+                # per step: the sweep kernel, and for the resident form the
+                # parameter-draws kernel before it
+                "gpu_launches": args.steps * (2 if form == "resident" else 1),
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": summarize_clocks(clk.rows),
                 "steady_state": steady, "fp64": fp64,
                 "rk4_maps_per_s": world * maps * NSKIP / (ms_per_step * 1e-3),

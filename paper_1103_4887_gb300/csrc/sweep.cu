@@ -258,6 +258,32 @@ __device__ __forceinline__ void site_draws(const Ctx& c, long long s, int64_t n,
     u = Num<R>::uni(w.x, w.y);
 }
 
+// The draws of site n's move at sweep s: the proposal increments z and
+// E = -log u of the accept uniform.
+template <class Model, class R>
+__device__ __forceinline__ void site_draw(const Ctx& c, long long s, int64_t n, R* z, R& E)
+{
+    R u;
+    site_draws<Model, R>(c, s, n, z, u);
+    E = neglog<R>(u);
+}
+
+// The proposal from its increments: x' = x + sigma z (one fma a component)
+// and its cached value.
+template <class Model, class R>
+__device__ __forceinline__ void site_propose_from(const Ctx& c, const Coef<R>& k, int64_t n, const R* pr,
+                                                  const R* x, const R* sg, R drive, const R* z, R* xp, R* gp)
+{
+    constexpr int D = Model::D;
+#pragma unroll
+    for (int a = 0; a < D; ++a) xp[a] = fma(sg[a], z[a], x[a]);
+    if (n < cache_len(c)) cache_value_at<Model, R>(c, k, xp, pr, drive, gp);
+    else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gp[a] = R(0);
+    }
+}
+
 // A site move from operands in registers, in two halves.  The proposal:
 // x' = x + sigma z, its cached value, and -log u of the accept uniform.
 template <class Model, class R>
@@ -265,16 +291,9 @@ __device__ __forceinline__ void site_propose(const Ctx& c, const Coef<R>& k, int
                                              const R* x, const R* sg, R drive, R* xp, R* gp, R& E)
 {
     constexpr int D = Model::D;
-    R z[D], u;
-    site_draws<Model, R>(c, s, n, z, u);
-    E = neglog<R>(u);
-#pragma unroll
-    for (int a = 0; a < D; ++a) xp[a] = x[a] + sg[a] * z[a];
-    if (n < cache_len(c)) cache_value_at<Model, R>(c, k, xp, pr, drive, gp);
-    else {
-#pragma unroll
-        for (int a = 0; a < D; ++a) gp[a] = R(0);
-    }
+    R z[D];
+    site_draw<Model, R>(c, s, n, z, E);
+    site_propose_from<Model, R>(c, k, n, pr, x, sg, drive, z, xp, gp);
 }
 
 // The decision: Delta A_n and the Metropolis rule written as dA < -log u
@@ -1002,6 +1021,12 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
     __syncthreads();
 
     bool odd_flag_wait = false;  // the previous sweep had no parameter barrier
+    // this site's draws of the next sweep, formed during the last parameter
+    // barrier of a sweep (they depend only on the counters)
+    R zn[D], En = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) zn[a] = R(0);
+    bool have_draws = false;
     for (int64_t k = 0; k < n_sweeps; ++k) {
         const long long s = sh.sweep;
         const unsigned long long ep = sh.ep0 + (unsigned long long)k + 1ull;
@@ -1022,8 +1047,15 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
             if (own && (int)(n & 1) == parity) {
                 // the proposal first: it needs no neighbour, so it overlaps the
                 // halo wait of the tile's boundary sites
-                R xp[D], gp[D], E;
-                site_propose<Model, R>(c, kc, n, s, pr, xr, sgr, drive, xp, gp, E);
+                R xp[D], gp[D], z[D], E;
+                if (have_draws) {
+#pragma unroll
+                    for (int a = 0; a < D; ++a) z[a] = zn[a];
+                    E = En;
+                } else {
+                    site_draw<Model, R>(c, s, n, z, E);
+                }
+                site_propose_from<Model, R>(c, kc, n, pr, xr, sgr, drive, z, xp, gp);
                 Nbhd<R, D> nb;
                 R xl[D], gl[D];
 #pragma unroll
@@ -1093,6 +1125,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
             if (Sync::tiled && tid == 0 && parity == 0) flag_post(c, 0, ep);
         }
 
+        have_draws = false;  // this sweep's draws are used
         {
             // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
             unsigned todo = 0u;
@@ -1260,6 +1293,12 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                                 sh.cta_spec[spec_buf][1] = r;
                             }
                         }
+                    } else if (own) {
+                        // the sweep's last move: the site threads have no
+                        // speculation to do during its barrier, so they draw
+                        // this site's move of the next sweep
+                        site_draw<Model, R>(c, s + 1, n, zn, En);
+                        have_draws = true;
                     }
                     __syncthreads();
                     if (sh.abort) goto done;
