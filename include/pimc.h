@@ -330,6 +330,19 @@ int pimc_debug_skip_arrive(pimc_t h, int cta);
  * >= 2^62 count as infinite, NaN gives NaN.  No handle; synchronous.
  * PIMC_ERR_ARG for n < 0 or n > 2^20, PIMC_ERR_CUDA on a device error. */
 int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out);
+/* The FP32 form of the model map f (one classical RK4 step of the HH field of
+ * Sec. 5.1 with the textbook rates, drive held over the step; the map of the
+ * model-error term of Eq. (action)) at n sites, for tests of its two lane
+ * forms: X (4*n doubles, component-major [a][n]), I_inj (n), p (7: gNa, gK,
+ * gL, ENa, EK, EL, C) and dt are host inputs, rounded to FP32 on the device;
+ * f_out (4*n doubles, host, caller-owned) receives the single-site map, and
+ * *n_mismatch the number of components of the sites (2i, 2i + 1), evaluated
+ * as the two lanes of one packed f32x2 map, whose bits differ from it.  No
+ * handle; synchronous; allocates and frees its device buffers.
+ * PIMC_ERR_ARG for n outside [1, 2^22], dt <= 0 or a NULL array,
+ * PIMC_ERR_CUDA on a device error. */
+int pimc_debug_lane_maps(const double* X, const double* I_inj, const double* p, double dt, int64_t n,
+                         double* f_out, int64_t* n_mismatch);
 /* Force the sweep grid size (0: automatic). */
 int pimc_set_grid(pimc_t h, int grid);
 

@@ -126,6 +126,8 @@ cudaError_t launch_param_delta(int model, int prec, const Ctx& c, int l, double 
                                double* out, cudaStream_t s);
 // Exact Fix3 sum of n device terms (as FP32 when as_float) into *out (device).
 cudaError_t launch_fix_sum(const double* t, int64_t n, int as_float, double* out, cudaStream_t s);
+cudaError_t launch_lane_maps(const double* X, const double* I, const double* p, double dt, int64_t n, double* out,
+                             unsigned* mismatch, cudaStream_t s);
 // dst[i] = (storage type) src[i], i < n.
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t s);
 // Ensemble forecast from the current state: out[e][a][k] (device, FP64).

@@ -969,6 +969,38 @@ int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out
     return PIMC_OK;
 }
 
+int pimc_debug_lane_maps(const double* X, const double* I_inj, const double* p, double dt, int64_t n, double* f_out,
+                         int64_t* n_mismatch)
+{
+    if (n < 1 || n > (1 << 22) || !X || !I_inj || !p || !f_out || !n_mismatch || !(dt > 0.0)) {
+        set_thread_error("pimc_debug_lane_maps: 1 <= n <= 2^22 sites, dt > 0 and all arrays are required");
+        return PIMC_ERR_ARG;
+    }
+    const size_t nx = sizeof(double) * 4 * (size_t)n, ni = sizeof(double) * (size_t)n, np = sizeof(double) * 8;
+    char* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * nx + ni + np + 256);
+    double* dX = (double*)d;
+    double* dF = (double*)(d + nx);
+    double* dI = (double*)(d + 2 * nx);
+    double* dp = (double*)(d + 2 * nx + ni);
+    unsigned* dm = (unsigned*)(d + 2 * nx + ni + np);
+    if (e == cudaSuccess) e = cudaMemcpy(dX, X, nx, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dI, I_inj, ni, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dp, p, sizeof(double) * 7, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dm, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = launch_lane_maps(dX, dI, dp, dt, n, dF, dm, 0);
+    unsigned m = 0u;
+    if (e == cudaSuccess) e = cudaMemcpy(f_out, dF, nx, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&m, dm, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        set_thread_error(cudaGetErrorString(e));
+        return PIMC_ERR_CUDA;
+    }
+    *n_mismatch = (int64_t)m;
+    return PIMC_OK;
+}
+
 int pimc_debug_skip_arrive(pimc_t h, int cta)
 {
     if (!h) return PIMC_ERR_ARG;

@@ -1674,6 +1674,54 @@ __global__ void __launch_bounds__(256) fix_sum_kernel(const double* t, int64_t n
     if (threadIdx.x == 0) *out = fix_value(s);
 }
 
+// The FP32 HH map (one RK4 step) of n sites in the single-lane form, written
+// to out[4][n] as FP64, and of the pairs (2i, 2i + 1) in the packed f32x2
+// form; *mismatch counts the pair components whose bits differ from the
+// single-lane map (the test hook of the lane form).
+__global__ void __launch_bounds__(256) lane_maps_kernel(const double* X, const double* I, const double* p, double dt,
+                                                        int64_t n, double* out, unsigned* mismatch)
+{
+    const int64_t n0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (n0 >= n) return;
+    const bool two = n0 + 1 < n;
+    float q[kMaxP];
+    HH<float>::prep(p, q);
+    const float dtf = (float)dt;
+    float x[2][4], f[2][4], drive[2];
+#pragma unroll
+    for (int L = 0; L < 2; ++L) {
+        const int64_t nn = (L == 1 && two) ? n0 + 1 : n0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[L][a] = (float)X[a * n + nn];
+        drive[L] = (float)I[nn];
+        rk4_map<HH<float>, float>(x[L], q, drive[L], dtf, f[L]);
+    }
+    float2 x2[4], q2[kMaxP], f2[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) x2[a] = make_float2(x[0][a], x[1][a]);
+#pragma unroll
+    for (int j = 0; j < kMaxP; ++j) q2[j] = splat<float2>(q[j]);
+    hh_rk4_lanes<float2>(x2, q2, make_float2(drive[0], drive[1]), splat<float2>(dtf),
+                         splat<float2>(__fmul_rn(0.5f, dtf)), splat<float2>(__fdiv_rn(dtf, 6.0f)), f2);
+    unsigned bad = 0u;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        bad += __float_as_uint(f2[a].x) != __float_as_uint(f[0][a]) ? 1u : 0u;
+        bad += (two && __float_as_uint(f2[a].y) != __float_as_uint(f[1][a])) ? 1u : 0u;
+        out[a * n + n0] = (double)f[0][a];
+        if (two) out[a * n + n0 + 1] = (double)f[1][a];
+    }
+    if (bad) atomicAdd(mismatch, bad);
+}
+
+cudaError_t launch_lane_maps(const double* X, const double* I, const double* p, double dt, int64_t n, double* out,
+                             unsigned* mismatch, cudaStream_t s)
+{
+    const int64_t pairs = (n + 1) / 2;
+    lane_maps_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(X, I, p, dt, n, out, mismatch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fix_sum(const double* t, int64_t n, int as_float, double* out, cudaStream_t s)
 {
     if (as_float) fix_sum_kernel<float><<<1, 256, 0, s>>>(t, n, out);

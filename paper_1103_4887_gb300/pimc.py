@@ -35,7 +35,7 @@ EXPORTS = [
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
-    "pimc_debug_skip_arrive", "pimc_debug_fix_sum", "pimc_set_grid", "pimc_action_static",
+    "pimc_debug_skip_arrive", "pimc_debug_fix_sum", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
     "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
 ]
@@ -117,6 +117,7 @@ def _declare(L):
         "pimc_set_wait_limit": [_vp, _i64],
         "pimc_debug_skip_arrive": [_vp, _int],
         "pimc_debug_fix_sum": [_vp, _i64, _int, _vp],
+        "pimc_debug_lane_maps": [_vp, _vp, _vp, _d, _i64, _vp, _vp],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
         "pimc_batch_create": [_vp, _vp, _int],
@@ -164,6 +165,22 @@ def debug_fix_sum(terms, as_float=False):
     if r != OK:
         raise PimcError(r, L.pimc_last_error(None).decode())
     return float(out[0])
+
+
+def debug_lane_maps(X, I, p, dt):
+    """FP32 HH maps of the sites (columns of X) in the single-site form, and the
+    number of pair components whose packed two-lane map differs (test hook)."""
+    L = load()
+    Xc = _f64(X).reshape(4, -1)
+    n = Xc.shape[1]
+    Ic, pc = _f64(I), _f64(p)
+    assert Ic.size == n and pc.size == 7
+    f = np.zeros((4, n))
+    m = np.zeros(1, dtype=np.int64)
+    r = L.pimc_debug_lane_maps(_p(Xc), _p(Ic), _p(pc), float(dt), int(n), _p(f), _p(m))
+    if r != OK:
+        raise PimcError(r, L.pimc_last_error(None).decode())
+    return f, int(m[0])
 
 
 class Sampler:
