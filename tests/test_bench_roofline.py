@@ -1,0 +1,44 @@
+"""The roofline denominators bench.py reports, against the arithmetic stated
+for them: the per-map cost of the FP32 HH RK4 map counted from its formula
+(4 field evaluations of 50 FP32 operations, 16 of them fmas, and 5 SFU
+operations; 28 stage combinations, 24 of them fmas), and the derived peak from
+the unit counts (FP32 lanes 128 and SFU 16 per clock and SM)."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_map_cost_matches_its_count(bench):
+    per_field_ops, per_field_fmas, per_field_sfu = 50, 16, 5
+    combos, combo_fmas = 28, 24
+    assert bench.FP32_OPS_PER_MAP == 4 * per_field_ops + combos
+    assert bench.MUFU_OPS_PER_MAP == 4 * per_field_sfu
+    # flops with an fma counted as two
+    assert bench.FLOP_PER_MAP == bench.FP32_OPS_PER_MAP + 4 * per_field_fmas + combo_fmas
+
+
+def test_derived_peak_is_fp32_bound(bench):
+    n_sm, mhz = 152, 2070.0
+    fp32_clk = bench.FP32_OPS_PER_MAP / 128.0
+    sfu_clk = bench.MUFU_OPS_PER_MAP / 16.0
+    assert fp32_clk > sfu_clk  # the map is bound by the FP32 lanes, not the SFU
+    peak = bench._peak_fp32_tflops(n_sm, mhz)
+    assert peak == pytest.approx(bench.FLOP_PER_MAP * n_sm * mhz * 1e6 / fp32_clk / 1e12, rel=1e-12)
+    assert peak == pytest.approx(55.8, abs=0.05)
+
+
+def test_maps_per_sweep(bench):
+    # one map per site and sweep for the state moves, one per site and free
+    # parameter for the parameter moves (sites 0..M-1 carry a map)
+    assert bench.maps_per_sweep(32768, 7) == 8 * 32768
