@@ -192,18 +192,24 @@ int pimc_grad_dev(pimc_t h, const double* X_dev, const double* p_dev, double bet
  * code held to a fixed memory budget or a caller-owned pool, plugin hosts
  * that forbid cudaMalloc/cudaFree on their threads, and real-time loops in
  * which an allocation (which may synchronise the device) is not allowed.
- * It computes the same FP64 action (A, A_o, A_f at beta = 1) as
- * pimc_action_dev, without a handle: X_dev (D*(M+1) doubles, SoA), p_dev
- * (Np), y_dev (M+1), I_dev (M) and out_dev (3 doubles) are caller-owned
- * device arrays, Rf (D doubles) is host memory; work is enqueued on `stream`.
+ * It computes the FP64 action (A, A_o, A_f at beta = 1) with the explicit
+ * RK4 model error, without a handle: the value pimc_action_dev gives for an
+ * FP64 handle with the RK4 scheme.  Supported models: PIMC_MODEL_HH,
+ * PIMC_MODEL_LINGAUSS and PIMC_MODEL_TOY1D; PIMC_MODEL_HH_PAPER (and the
+ * trapezoid scheme, which has no argument here) are not, and that model
+ * returns PIMC_ERR_ARG.  X_dev (D*(M+1) doubles, SoA), p_dev (Np), y_dev
+ * (M+1), I_dev (M) and out_dev (3 doubles) are caller-owned device arrays;
+ * Rf is host memory holding exactly D doubles (the model's dimension); work
+ * is enqueued on `stream`.
  * Its scratch (per-CTA partial sums and a last-block counter, 33,024 bytes)
  * is one fixed array in device memory that every GPU loading this library
  * holds until the process exits, so M is limited to 1 <= M <= 262,143;
  * larger M (and bad pointers or sizes) return PIMC_ERR_ARG with a message in
  * pimc_last_error(NULL).  It calls no cudaMalloc, cudaFree or other
- * allocating routine.  The first call on a device looks up the array's
- * device address on that device (make that first call before any stream
- * capture).  Every call shares the array: calls that overlap on the GPU
+ * allocating routine.  Every call looks up the array's device address in
+ * the current context (cudaGetSymbolAddress, which allocates nothing); the
+ * first call on a device may also load the library's device code there, so
+ * make that first call before any stream capture.  Every call shares the array: calls that overlap on the GPU
  * (different streams, devices excepted) race and must be serialised by the
  * caller. */
 int pimc_action_static(int model, int64_t M, double dt, double Rm, const double* Rf,

@@ -4,12 +4,11 @@
 // under a fixed memory budget or a caller-owned memory pool, plugin hosts that
 // forbid cudaMalloc/cudaFree on their threads, and real-time loops where an
 // allocation (which may synchronise the device) is not allowed.  For them,
-// pimc_action_static computes the same FP64 action as pimc_action_dev without
-// a handle and without allocating: its per-CTA partial sums and its
+// pimc_action_static computes the FP64 action of the explicit RK4 model error
+// (what pimc_action_dev gives for an FP64 handle with the RK4 scheme and model
+// HH, LINGAUSS or TOY1D) without a handle and without allocating: its per-CTA partial sums and its
 // last-block counter live in one file-scope __device__ array, held by every
 // GPU that loads this library until the process exits.
-#include <mutex>
-
 #include <cstdio>
 
 #include "../../include/pimc.h"
@@ -27,10 +26,6 @@ constexpr size_t kScratchBytes = kCounterBytes + sizeof(double) * 2 * kStaticMax
 
 // The shared scratch: counter, then 2 doubles (A_o, A_f) per CTA.
 static __device__ __align__(256) unsigned char g_action_scratch[kScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
 template <class Model>
 __global__ void __launch_bounds__(kStaticBlock)
@@ -93,26 +88,23 @@ action_static_kernel(int64_t M, double dt, double Rm, double Rf0, double Rf1, do
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// Device address of the scratch array in the current device's context.  It is
+// looked up on every call (cudaGetSymbolAddress allocates nothing and costs a
+// table lookup): an address cached from an earlier call would belong to a
+// context that no longer exists after cudaDeviceReset, or that is not current
+// when the caller has made another context current.
 int scratch_address(void** ptr)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        set_thread_error("pimc_action_static: no usable current CUDA device");
+    void* a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, g_action_scratch);
+    if (e != cudaSuccess || !a) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "pimc_action_static: cudaGetSymbolAddress of the scratch array failed: %s",
+                 cudaGetErrorString(e));
+        set_thread_error(msg);
         return PIMC_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* a = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&a, g_action_scratch);
-        if (e != cudaSuccess || !a) {
-            set_thread_error("pimc_action_static: cudaGetSymbolAddress of the scratch array failed");
-            return PIMC_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = a;
-    }
-    *ptr = g_scratch_addr[dev];
+    *ptr = a;
     return PIMC_OK;
 }
 
@@ -129,6 +121,10 @@ extern "C" int pimc_action_static(int model, int64_t M, double dt, double Rm, co
     case PIMC_MODEL_HH: D = 4; break;
     case PIMC_MODEL_LINGAUSS: D = 2; break;
     case PIMC_MODEL_TOY1D: D = 1; break;
+    case PIMC_MODEL_HH_PAPER:
+        set_thread_error("pimc_action_static: PIMC_MODEL_HH_PAPER is not supported by this entry point "
+                         "(models HH, LINGAUSS and TOY1D with the RK4 model error only)");
+        return PIMC_ERR_ARG;
     default: set_thread_error("pimc_action_static: unknown model"); return PIMC_ERR_ARG;
     }
     if (M < 1 || M > kStaticMaxM) {

@@ -147,9 +147,13 @@ def _f64(a):
 
 
 def action_static(model, M, dt, Rm, Rf, X_ptr, p_ptr, y_ptr, I_ptr, out_ptr, stream_ptr):
-    """Allocation-free FP64 action of caller-owned device arrays (no handle)."""
+    """Allocation-free FP64 action of caller-owned device arrays (no handle).
+    Rf must hold exactly D doubles for the model: the library reads D of them."""
     L = load()
-    rf = _f64(Rf)
+    rf = _f64(Rf).ravel()
+    if int(model) not in MODEL_DIMS or rf.size != MODEL_DIMS[int(model)][0]:
+        raise PimcError(ERR_ARG, f"Rf must hold D = {MODEL_DIMS.get(int(model), ('?',))[0]} values for model "
+                                 f"{model}, got {rf.size}")
     r = L.pimc_action_static(int(model), int(M), float(dt), float(Rm), _p(rf), _vp(X_ptr), _vp(p_ptr),
                              _vp(y_ptr), _vp(I_ptr), _vp(out_ptr), _vp(stream_ptr))
     if r != OK:
