@@ -4,10 +4,14 @@ Each chain of a batch runs exactly the sweeps it runs alone on one CTA
 (pimc_set_grid(h, 1)): states, parameters and moments are bit-identical.
 Counters are keyed by the chain id, never by the CTA, so the assignment of
 chains to CTAs (the tiling, the autotuner's choice) does not change a chain.
+Chains of a batch are also replayed against the FP64 oracle sweep by sweep
+(the rule of the single-chain replays: a differing decision must sit within
+1e-9 of its threshold, Eq. (Paccept), and is counted).
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1103_4887_gb300 import pimc, synth
 
 pytestmark = pytest.mark.gpu
@@ -82,3 +86,68 @@ def test_autotune_picks_a_valid_shape():
     b.sweep(5, 2)
     for s in chains:
         assert np.all(np.isfinite(s.state()[0]))
+
+
+def test_batched_chains_replay_against_oracle():
+    """The shortest and the longest chain of an FP64 batch (M = 37 and 5000,
+    3 and 7 free parameters, chain ids 0 and 5) follow the oracle chain with
+    the same data, steps and chain id, one batched sweep at a time."""
+    Ms = [37, 800, 2500, 64, 1200, 5000]
+    probs, samplers = [], []
+    for k, M in enumerate(Ms):
+        prob = synth.hh_problem(M, data_seed=300 + k, free="all" if k % 2 else ("gNa", "gK", "gL"))
+        s = pimc.Sampler.from_problem(prob)
+        s.set_chain(k)
+        probs.append(prob)
+        samplers.append(s)
+    b = pimc.Batch(samplers)
+    b.set_tuning(256, 0)
+    watch = [0, 5]
+    oracles = {}
+    for k in watch:
+        prob = probs[k]
+        o = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf)
+        o.set_data(prob.y, prob.I)
+        o.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
+        o.set_steps(prob.sig_x, prob.sig_p)
+        o.set_chain(k)
+        oracles[k] = o
+    flips = {k: 0 for k in watch}
+    moves = {k: 0 for k in watch}
+    seed = 31
+    for s_idx in range(40):
+        before = {k: samplers[k].state() for k in watch}
+        for k in watch:
+            X0, p0 = before[k]
+            o = oracles[k]
+            o.set_path(X0)
+            o.set_params(p0, probs[k].lo, probs[k].hi, probs[k].free)
+            o.set_sweep_counter(s_idx, 1.0)
+        b.sweep(1, seed)
+        for k in watch:
+            prob, o = probs[k], oracles[k]
+            X0, p0 = before[k]
+            o.sweep(1, seed)
+            Xg, pg = samplers[k].state()
+            Xo, po = o.state()
+            sm, pm = o.last_margins()
+            moved_g = np.any(Xg != X0, axis=0)
+            moved_o = np.any(Xo != X0, axis=0)
+            differ = moved_g != moved_o
+            moves[k] += int(np.sum(moved_g))
+            if np.any(differ):
+                assert np.all(sm[differ] < 1e-9), (k, s_idx, np.where(differ)[0])
+                flips[k] += int(np.sum(differ))
+            same = ~differ
+            tol = 1e-12 * np.maximum(1.0, np.abs(Xo))
+            assert np.all(np.abs(Xg - Xo)[:, same] <= tol[:, same]), (k, s_idx)
+            for l in range(prob.Np):
+                if (pg[l] != p0[l]) != (po[l] != p0[l]):
+                    assert pm[l] < 1e-9, (k, s_idx, l)
+                    flips[k] += 1
+                else:
+                    assert abs(pg[l] - po[l]) <= 1e-12 * max(1.0, abs(po[l]))
+    for k in watch:
+        assert flips[k] <= 2, (k, flips[k])
+        assert moves[k] > 0
+        assert samplers[k].sweep_counter()[0] == 40

@@ -5,8 +5,8 @@ the closed-form linear-Gaussian posterior.
   state; accept decisions must agree (a differing decision must sit within
   1e-9 of its threshold) and accepted end points must agree to the leapfrog's
   rounding (FP64).
-* T-LG: means and variances of GPU HMC chains match the closed form (FP64
-  and FP32-mixed).
+* T-LG: means and variances of 32 independent GPU HMC chains match the closed
+  form within 4 standard errors (FP64 and FP32-mixed).
 """
 import numpy as np
 import pytest
@@ -81,7 +81,7 @@ def test_hmc_T_LG_closed_form(precision):
     mu, cov = lgc.posterior(L, r, w)
     inv_mass = np.diag(cov).copy()
     means, vars_ = [], []
-    for k in range(8):
+    for k in range(32):
         g = pimc.Sampler.from_problem(prob, precision=pimc.FP64 if precision == "fp64" else pimc.FP32_MIXED)
         g.set_chain(k)
         g.set_schedule(n_init=200, n_skip=1)
@@ -91,11 +91,12 @@ def test_hmc_T_LG_closed_form(precision):
         assert J == 6000
         means.append(m)
         vars_.append(v)
+        g.close()
     means, vars_ = np.array(means), np.array(vars_)
     se_m = means.std(0, ddof=1) / np.sqrt(len(means))
     se_v = vars_.std(0, ddof=1) / np.sqrt(len(vars_))
-    assert np.all(np.abs(means.mean(0) - mu) < 4.5 * se_m)
-    assert np.all(np.abs(vars_.mean(0) - np.diag(cov)) < 4.5 * se_v)
+    assert np.all(np.abs(means.mean(0) - mu) < 4 * se_m)
+    assert np.all(np.abs(vars_.mean(0) - np.diag(cov)) < 4 * se_v)
 
 
 def test_param_trace_matches_per_sweep_state():
