@@ -40,9 +40,21 @@ PAPER_SPEEDUP_CONTEXT = ("T_CPU/T_GPU up to about 300 (GTX 470, 448 cores) and 2
                          "Intel Core i3 core, FP32, M = 100..40000, 1e5 sweeps")
 SEED = 1
 REF_BUDGET_S = 120.0
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum) of one 10-sweep launch of
-# the resident sweep kernel on this workload, cold cache
-RESIDENT_STEP_DRAM_BYTES = 7.861e6
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold cache)
+# of one launch of a sweep kernel, with the hash of the kernel sources it was
+# captured on: a figure is reported only while the sources still hash the same
+# (a changed kernel has no traffic figure until it is captured again).
+KERNEL_SOURCES = ("paper_1103_4887_gb300/csrc/sweep.cu", "paper_1103_4887_gb300/csrc/device.cuh",
+                  "paper_1103_4887_gb300/csrc/scheme.cuh", "paper_1103_4887_gb300/csrc/stats.cuh",
+                  "paper_1103_4887_gb300/csrc/internal.h")
+TRAFFIC = {
+    # one 10-sweep bench step of sweep_resident_kernel<HH<float>>, M = 32768
+    ("resident", 32768): {"bytes": 7.861e6, "sweeps": 10, "src": "uncaptured",
+                          "profile": "profiles/sweep_resident_kernel_hh_M32768_full.md"},
+    # one 10-sweep launch of sweep_kernel<HH<float>,float>, M = 2^20
+    ("general", 1048576): {"bytes": 593.0e6, "sweeps": 10, "src": "uncaptured",
+                           "profile": "profiles/sweep_kernel_hh_M1048576_full.md"},
+}
 
 # Algorithmic cost of one RK4 map of the HH vector field in the FP32-mixed
 # form, counted from the formula (4 field evaluations of 50 FP32 operations
@@ -53,11 +65,48 @@ FP32_OPS_PER_MAP = 228
 MUFU_OPS_PER_MAP = 20
 # FP32 floating-point operations per map (an FMA counted as 2).
 FLOP_PER_MAP = 316
+# The scope table's own count of one RK4 map of the HH field (6 exponentials and
+# 3-4 divides per field evaluation): 24 ex2 and 14 rcp on the SFU, about 250
+# FP32 flop; at 16 SFU operations per clock and SM it is SFU-bound.
+SURVEY_SFU_OPS_PER_MAP = 38
+SURVEY_FLOP_PER_MAP = 250
 
 
 def maps_per_sweep(M, n_free):
     # one map per site move (sites 0..M-1 have a successor) and M per free parameter
     return M * (1 + n_free)
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(form, M, n_sweeps):
+    """DRAM bytes of one launch of n_sweeps sweeps from the recorded capture,
+    scaled by the sweeps (a launch's traffic grows with its sweeps), or None
+    when there is no capture for this kernel and size, or the kernel sources
+    changed since it was taken."""
+    rec = TRAFFIC.get((form, M))
+    if rec is None or rec["src"] != kernel_source_hash():
+        return None
+    return rec["bytes"] * n_sweeps / rec["sweeps"]
+
+
+def roofline_fracs(maps, seconds, n_sm, sm_mhz):
+    """Fractions of the FP32/SFU compute roofline reached by `maps` RK4 maps in
+    `seconds`: against the map's recount (228 FP32 + 20 SFU operations,
+    FP32-bound) and against the scope table's count (24 ex2 + 14 rcp on the
+    SFU, SFU-bound)."""
+    f = sm_mhz * 1e6
+    t_recount = maps * max(FP32_OPS_PER_MAP / 128.0, MUFU_OPS_PER_MAP / 16.0) / (n_sm * f)
+    t_survey = maps * max(SURVEY_FLOP_PER_MAP / 2.0 / 128.0, SURVEY_SFU_OPS_PER_MAP / 16.0) / (n_sm * f)
+    return {"frac_recount": t_recount / seconds, "frac_survey_count": t_survey / seconds,
+            "t_min_recount_s": t_recount, "t_min_survey_count_s": t_survey}
 
 
 class ClockSampler:
@@ -217,18 +266,20 @@ def _peak_fp32_tflops(n_sm, sm_mhz):
     return FLOP_PER_MAP / t_map / 1e12
 
 
-def run_sweep_M(args):
+def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0):
     """Observation-length sweep (HH, all 7 parameters free): per M, device time
     per sweep in one persistent launch (state L2-resident between sweeps, as in
-    a sampling run), FP32-mixed and FP64, and the serial oracle on one host core
-    for a bounded number of sweeps."""
+    a sampling run), FP32-mixed and FP64, and the oracle timed on the host for a
+    bounded number of sweeps -- the serial build on one core and the OpenMP
+    build on all cores (its thread count stated)."""
     import torch
     import oracle
     from paper_1103_4887_gb300 import pimc, synth
-    peaks, _ = load_peaks()
+    peaks, peak_src = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    for e in range(10, 21, 2):
+    rows = []
+    for e in exps:
         M = 1 << e
         prob = synth.hh_problem(M, data_seed=0, free="all")
         row = {"M": M}
@@ -247,34 +298,59 @@ def run_sweep_M(args):
             s.sync()
             ms = e0.elapsed_time(e1) / n
             maps = maps_per_sweep(M, 7)
-            tf = maps * FLOP_PER_MAP / (ms * 1e-3) / 1e12
-            peak = _peak_fp32_tflops(n_sm, sm_mhz) if prec == pimc.FP32_MIXED else 1.25
-            row[name] = {"ms_per_sweep": ms, "site_updates_per_s": (M + 1) / (ms * 1e-3),
-                         "rk4_maps_per_s": maps / (ms * 1e-3), "achieved_tflops": tf, "roofline_frac": tf / peak,
-                         "grid_block": list(s.launch_info())}
+            form = s.sweep_form()
+            entry = {"ms_per_sweep": ms, "site_updates_per_s": (M + 1) / (ms * 1e-3),
+                     "rk4_maps_per_s": maps / (ms * 1e-3), "sweeps_timed": n, "form": form,
+                     "grid_block": list(s.launch_info())}
+            if prec == pimc.FP32_MIXED:
+                tf = maps * FLOP_PER_MAP / (ms * 1e-3) / 1e12
+                entry.update({"achieved_tflops": tf, **roofline_fracs(maps, ms * 1e-3, n_sm, sm_mhz)})
+                tr = traffic_of(form, M, 10)
+                if tr is not None:
+                    entry["traffic_bytes_per_10_sweeps"] = tr
+                    entry["dram_gbs"] = tr / (10 * ms * 1e-3) / 1e9
+            else:
+                # FP64 transcendental functions are software sequences on the FP64
+                # pipe: the achieved rate is stated as maps/s; the FP32 count does
+                # not apply
+                entry["note"] = "FP64 pipe-bound (software exp); compare maps/s"
+            row[name] = entry
             s.close()
         n_cpu = 100 if M <= 1 << 12 else (10 if M <= 1 << 16 else 2)
         for key, omp in (("oracle_1core", False), ("oracle_allcores", True)):
             try:
                 ch = oracle.Chain(prob.model, prob.M, prob.dt, prob.Rm, prob.Rf, openmp=omp)
-            except Exception as e:  # no OpenMP build on this host
-                row[key] = {"error": repr(e)}
+            except Exception as ex:  # no OpenMP build on this host
+                row[key] = {"error": repr(ex)}
                 continue
             ch.set_data(prob.y, prob.I)
             ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
             ch.set_steps(prob.sig_x, prob.sig_p)
             t0 = time.perf_counter()
-            ch.sweep(n_cpu, SEED)
-            cpu_s = (time.perf_counter() - t0) / n_cpu
-            row[key] = {"s_per_sweep": cpu_s, "site_updates_per_s": (M + 1) / cpu_s, "sweeps_timed": n_cpu,
-                        "threads": oracle.threads(omp)}
+            k = 0
+            while k < n_cpu:
+                ch.sweep(1, SEED)
+                k += 1
+                if time.perf_counter() - t0 > cpu_budget_s:
+                    break
+            cpu_s = (time.perf_counter() - t0) / k
+            row[key] = {"s_per_sweep": cpu_s, "site_updates_per_s": (M + 1) / cpu_s, "sweeps_timed": k,
+                        "threads": oracle.threads(omp), "nproc": os.cpu_count()}
         cpu_s = row["oracle_1core"]["s_per_sweep"]
-        row["speedup_fp32_vs_oracle"] = cpu_s / (row["fp32mixed"]["ms_per_sweep"] * 1e-3)
-        row["speedup_fp64_vs_oracle"] = cpu_s / (row["fp64"]["ms_per_sweep"] * 1e-3)
+        row["speedup_fp32_vs_oracle_1core"] = cpu_s / (row["fp32mixed"]["ms_per_sweep"] * 1e-3)
+        row["speedup_fp64_vs_oracle_1core"] = cpu_s / (row["fp64"]["ms_per_sweep"] * 1e-3)
         if "s_per_sweep" in row["oracle_allcores"]:
             row["speedup_fp32_vs_oracle_allcores"] = (row["oracle_allcores"]["s_per_sweep"]
                                                       / (row["fp32mixed"]["ms_per_sweep"] * 1e-3))
-        row["paper_speedup_context"] = PAPER_SPEEDUP_CONTEXT
+        rows.append(row)
+    return {"rows": rows, "paper_speedup_context": PAPER_SPEEDUP_CONTEXT,
+            "peak_clock": f"{sm_mhz:.0f} MHz ({peak_src})", "n_sm": n_sm,
+            "frac_recount": "maps x max(228/128, 20/16) clocks / (SMs x clock) / time",
+            "frac_survey_count": "maps x max(125/128, 38/16) clocks / (SMs x clock) / time"}
+
+
+def run_sweep_M(args):
+    for row in sweep_M_rows(cpu_budget_s=30.0)["rows"]:
         print(json.dumps(row), flush=True)
 
 
@@ -687,12 +763,15 @@ def main():
     achieved = maps * NSKIP * FLOP_PER_MAP / (ms_per_step * 1e-3) / 1e12
     kname = "sweep_resident_kernel<HH>" if form == "resident" else "sweep_kernel<HH>"
     # DRAM bytes (read + write) of one bench-step launch of this kernel, from
-    # an ncu capture of it on this workload
-    traffic = RESIDENT_STEP_DRAM_BYTES if (form == "resident" and args.M == M_DEFAULT
-                                           and prec == pimc.FP32_MIXED) else None
+    # an ncu capture of it on this workload (None once the kernel changed)
+    traffic = traffic_of(form, args.M, NSKIP) if prec == pimc.FP32_MIXED else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
-            "kernel": kname, "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)"}
+            "kernel": kname, "peak_source": f"derived from unit counts at {sm_mhz:.0f} MHz ({peak_src} clocks)",
+            "kernel_src_hash": kernel_source_hash()}
+    if prec == pimc.FP32_MIXED:
+        roof.update({k: v for k, v in roofline_fracs(maps * NSKIP, ms_per_step * 1e-3, n_sm, sm_mhz).items()
+                     if k.startswith("frac_")})
     if traffic is not None:  # the memory side of the same launch, against the copy peak
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roof["dram_gbs"] = traffic / (ms_per_step * 1e-3) / 1e9
@@ -705,6 +784,10 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not args.quick:
         samp.close()
+        try:
+            extras["sweep_M"] = sweep_M_rows()
+        except Exception as e:  # reported, not hidden
+            extras["sweep_M"] = {"error": repr(e)}
         try:
             extras["batch"] = run_batch(args)
         except Exception as e:  # reported, not hidden

@@ -42,3 +42,24 @@ def test_maps_per_sweep(bench):
     # one map per site and sweep for the state moves, one per site and free
     # parameter for the parameter moves (sites 0..M-1 carry a map)
     assert bench.maps_per_sweep(32768, 7) == 8 * 32768
+
+
+def test_survey_count_fraction(bench):
+    # the scope table's count: 24 ex2 + 14 rcp a map on 16 SFU lanes per clock
+    # and SM is the binding unit (its ~250 flop take fewer FP32 clocks)
+    maps, t, n_sm, mhz = 10 * 8 * 32768, 242e-6, 152, 2070.0
+    fr = bench.roofline_fracs(maps, t, n_sm, mhz)
+    t_sfu = maps * 38 / (16 * n_sm * mhz * 1e6)
+    assert fr["frac_survey_count"] == pytest.approx(t_sfu / t, rel=1e-12)
+    t_fp32 = maps * 228 / (128 * n_sm * mhz * 1e6)
+    assert fr["frac_recount"] == pytest.approx(t_fp32 / t, rel=1e-12)
+
+
+def test_traffic_only_for_the_captured_kernel_sources(bench, monkeypatch):
+    rec = {("resident", 32768): {"bytes": 8.0e6, "sweeps": 10, "src": bench.kernel_source_hash(), "profile": "x"}}
+    monkeypatch.setattr(bench, "TRAFFIC", rec)
+    assert bench.traffic_of("resident", 32768, 10) == pytest.approx(8.0e6)
+    assert bench.traffic_of("resident", 32768, 20) == pytest.approx(16.0e6)
+    assert bench.traffic_of("general", 32768, 10) is None
+    rec[("resident", 32768)]["src"] = "0" * 16
+    assert bench.traffic_of("resident", 32768, 10) is None
