@@ -333,7 +333,9 @@ int pimc_debug_skip_arrive(pimc_t h, int cta);
  * to n caller terms (host array, copied): *out = the sum of terms[0..n), each
  * first rounded to FP32 when as_float != 0, computed on the current device in
  * 42-bit integer chunks of 2^-64 and rounded once to FP64; terms of magnitude
- * >= 2^62 count as infinite, NaN gives NaN.  No handle; synchronous.
+ * >= 2^62 count as infinite, NaN gives NaN.  as_float == 2 adds the FP32
+ * terms through the per-thread 128-bit accumulator the parameter moves of the
+ * general sweep form use (same result).  No handle; synchronous.
  * PIMC_ERR_ARG for n < 0 or n > 2^20, PIMC_ERR_CUDA on a device error. */
 int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out);
 /* The FP32 form of the model map f (one classical RK4 step of the HH field of

@@ -32,7 +32,9 @@ __device__ __forceinline__ void accumulate(const Ctx& c, int64_t ci, double v, b
 // the current cache (f(x_n) or F(x_n)), which gives the model-error residuals
 // eps_{n+1} without another map evaluation; the
 // measurement residuals are delta_n = x_{n,0} - y_n (their statistics are the
-// model check of Sec. 6).
+// model check of Sec. 6).  Per site, every operand is loaded before any sum
+// is stored: the compiler cannot tell the arrays apart, and interleaved
+// read-modify-writes would cost one memory round trip per array.
 template <class Model, class R>
 __device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_here, const double* p,
                               bool first_rec, int t, int nt, const R* Fc)
@@ -40,24 +42,47 @@ __device__ void record_sample(const Ctx& c, int64_t n0, int64_t n1, bool params_
     constexpr int D = Model::D, NP = Model::NP;
     const int64_t M = c.M, nx = (int64_t)D * (M + 1);
     const R* X = (const R*)c.X;
+    const bool trap = c.scheme != kSchemeRK4;
     for (int64_t n = n0 + t; n < n1; n += nt) {
+        const bool has_eps = n < M, has_d = n >= 1;
+        double xv[D], sv[D], s1[D], s2[D], e[D + 1], r1[D + 1], r2[D + 1];
 #pragma unroll
-        for (int a = 0; a < D; ++a) accumulate(c, (int64_t)a * (M + 1) + n, (double)X[a * c.ldx + n], first_rec);
-        if (n < M) {
-            const bool trap = c.scheme != kSchemeRK4;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const double xn = (double)X[a * c.ldx + n], xn1 = (double)X[a * c.ldx + n + 1];
+        for (int a = 0; a < D; ++a) {
+            const int64_t ci = (int64_t)a * (M + 1) + n;
+            xv[a] = (double)X[a * c.ldx + n];
+            sv[a] = first_rec ? xv[a] : c.shift[ci];
+            s1[a] = c.S1[ci];
+            s2[a] = c.S2[ci];
+            e[a] = r1[a] = r2[a] = 0.0;
+            if (has_eps) {
+                const double xn1 = (double)X[a * c.ldx + n + 1];
                 const double gn = (double)Fc[a * c.ldf + n];
-                const double e = trap ? xn1 - xn - 0.5 * c.dt * ((double)Fc[a * c.ldf + n + 1] + gn) : xn1 - gn;
-                c.R1[(int64_t)a * M + n] += e;
-                c.R2[(int64_t)a * M + n] += e * e;
+                e[a] = trap ? xn1 - xv[a] - 0.5 * c.dt * ((double)Fc[a * c.ldf + n + 1] + gn) : xn1 - gn;
+                r1[a] = c.R1[(int64_t)a * M + n];
+                r2[a] = c.R2[(int64_t)a * M + n];
             }
         }
-        if (n >= 1) {
-            const double d = (double)X[n] - (double)((const R*)c.y)[n];
-            c.R1[(int64_t)D * M + n - 1] += d;
-            c.R2[(int64_t)D * M + n - 1] += d * d;
+        e[D] = r1[D] = r2[D] = 0.0;
+        if (has_d) {
+            e[D] = xv[0] - (double)((const R*)c.y)[n];
+            r1[D] = c.R1[(int64_t)D * M + n - 1];
+            r2[D] = c.R2[(int64_t)D * M + n - 1];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int64_t ci = (int64_t)a * (M + 1) + n;
+            const double d = xv[a] - sv[a];
+            if (first_rec) c.shift[ci] = sv[a];
+            c.S1[ci] = s1[a] + d;
+            c.S2[ci] = s2[a] + d * d;
+            if (has_eps) {
+                c.R1[(int64_t)a * M + n] = r1[a] + e[a];
+                c.R2[(int64_t)a * M + n] = r2[a] + e[a] * e[a];
+            }
+        }
+        if (has_d) {
+            c.R1[(int64_t)D * M + n - 1] = r1[D] + e[D];
+            c.R2[(int64_t)D * M + n - 1] = r2[D] + e[D] * e[D];
         }
     }
     if (params_here && t < NP) accumulate(c, nx + t, p[t], first_rec);

@@ -520,6 +520,50 @@ __device__ __forceinline__ bool fix_less(Fix3 s, double e)
     return s.c[0] < t.c[0];
 }
 
+// A thread's running exact sum of FP32 terms, for loops over many sites: the
+// same integer T = t 2^64 truncated toward zero as fix_add, kept as one
+// 128-bit two's complement integer (hi:lo) -- a shift and a 128-bit add or
+// subtract a term instead of a split into three chunks.  Terms of magnitude
+// 2^36 or more, and non-finite ones, go to the Fix3 sum instead, so up to 2^26
+// terms cannot overflow; acc_fold adds the 128-bit sum into the Fix3 sum.  The
+// total is the same integer either way, so every form keeps the same bits.
+struct Acc128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void acc_add(Acc128& a, Fix3& big, float t)
+{
+    const unsigned b = __float_as_uint(t);
+    const unsigned ex = (b >> 23) & 0xffu;
+    if (ex >= 127u + 36u) {
+        fix_add(big, t);
+        return;
+    }
+    const unsigned long long man = ex ? (unsigned long long)((b & 0x7fffffu) | 0x800000u) : (unsigned long long)(b & 0x7fffffu);
+    const int sh = (ex ? (int)ex - 150 : -149) + 64;  // bit of T that man's bit 0 lands on (<= 77)
+    unsigned long long lo = 0ull, hi = 0ull;
+    if (sh >= 64) hi = man << (sh - 64);
+    else if (sh > 40) { lo = man << sh; hi = man >> (64 - sh); }
+    else if (sh >= 0) lo = man << sh;
+    else if (sh > -24) lo = man >> (-sh);
+    if (b >> 31) {
+        const unsigned long long l2 = a.lo - lo;
+        a.hi = a.hi - hi - (a.lo < lo ? 1ull : 0ull);
+        a.lo = l2;
+    } else {
+        const unsigned long long l2 = a.lo + lo;
+        a.hi = a.hi + hi + (l2 < lo ? 1ull : 0ull);
+        a.lo = l2;
+    }
+}
+
+__device__ __forceinline__ void acc_fold(const Acc128& a, Fix3& f)
+{
+    f.c[0] += (long long)(a.lo & (unsigned long long)kFixMask);
+    f.c[1] += (long long)(((a.lo >> 42) | (a.hi << 22)) & (unsigned long long)kFixMask);
+    f.c[2] += (long long)a.hi >> 20;
+}
+
 // Warp sum of Fix3 values, valid in every lane.  Each lane's value is
 // normalised (c0, c1 in [0, 2^42)) and cut into 21-bit pieces -- the top
 // chunk's upper piece signed -- whose 32-lane sums fit 32-bit integers, so the
@@ -796,6 +840,7 @@ __device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<floa
     for (int j = 0; j < kMaxP; ++j) q2[j] = splat<float2>(pq[j]);
     const float2 dt2 = splat<float2>(k.dt), beta2 = splat<float2>(beta);
     const float2 hdt2 = splat<float2>(__fmul_rn(0.5f, k.dt)), sdt2 = splat<float2>(__fdiv_rn(k.dt, 6.0f));
+    Acc128 acc{0ull, 0ull};
     for (int64_t n = n0 + 2 * (int64_t)threadIdx.x; n < nend; n += 2 * NT) {
         const bool two = n + 1 < nend;
         float2 x[4], xn1[4], fc[4], fp[4];
@@ -812,9 +857,10 @@ __device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<floa
             else Fn[a * c.ldf + n] = fp[a].x;
         }
         const float2 t = rk4_term_lanes<float2, 4>(beta2, k.Rf, xn1, fp, fc);
-        fix_add(part, t.x);
-        if (two) fix_add(part, t.y);
+        acc_add(acc, part, t.x);
+        if (two) acc_add(acc, part, t.y);
     }
+    acc_fold(acc, part);
 }
 
 // ---- general form -----------------------------------------------------------
@@ -1183,6 +1229,11 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     const unsigned slot = sh.nred % 3u;
                     Fix3 cta;
                     if (spec_sums) {
+                        // before the sweep's last barrier, the site threads'
+                        // cache stores of this move (after the decision
+                        // before) are ordered ahead of the arrival: the next
+                        // sweep's halo reads of other CTAs rely on that barrier
+                        if (l2 < 0) __syncthreads();
                         fix_zero(cta);
                         if (tid == 0) cta = sh.cta_spec[spec_buf][sh.last_acc ? 0 : 1];
                         spec_buf ^= 1;
@@ -1662,14 +1713,22 @@ __global__ void __launch_bounds__(kBlock) param_delta_kernel(Ctx c, int l, doubl
     }
 }
 
-// The exact sum of n terms by one CTA (the test hook of the Fix3 arithmetic).
-template <class T>
+// The exact sum of n terms by one CTA (the test hook of the Fix3 arithmetic;
+// acc128: FP32 terms through the per-thread 128-bit accumulator, as the
+// general form's parameter moves add them).
+template <class T, bool acc128>
 __global__ void __launch_bounds__(256) fix_sum_kernel(const double* t, int64_t n, double* out)
 {
     __shared__ Fix3 wfix[256 / 32];
     Fix3 f;
     fix_zero(f);
-    for (int64_t i = threadIdx.x; i < n; i += 256) fix_add(f, (T)t[i]);
+    if constexpr (acc128) {
+        Acc128 a{0ull, 0ull};
+        for (int64_t i = threadIdx.x; i < n; i += 256) acc_add(a, f, (float)t[i]);
+        acc_fold(a, f);
+    } else {
+        for (int64_t i = threadIdx.x; i < n; i += 256) fix_add(f, (T)t[i]);
+    }
     const Fix3 s = fix_cta_sum<256>(f, wfix);
     if (threadIdx.x == 0) *out = fix_value(s);
 }
@@ -1724,8 +1783,9 @@ cudaError_t launch_lane_maps(const double* X, const double* I, const double* p, 
 
 cudaError_t launch_fix_sum(const double* t, int64_t n, int as_float, double* out, cudaStream_t s)
 {
-    if (as_float) fix_sum_kernel<float><<<1, 256, 0, s>>>(t, n, out);
-    else fix_sum_kernel<double><<<1, 256, 0, s>>>(t, n, out);
+    if (as_float == 2) fix_sum_kernel<float, true><<<1, 256, 0, s>>>(t, n, out);
+    else if (as_float) fix_sum_kernel<float, false><<<1, 256, 0, s>>>(t, n, out);
+    else fix_sum_kernel<double, false><<<1, 256, 0, s>>>(t, n, out);
     return cudaGetLastError();
 }
 

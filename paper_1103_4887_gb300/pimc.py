@@ -160,12 +160,14 @@ def action_static(model, M, dt, Rm, Rf, X_ptr, p_ptr, y_ptr, I_ptr, out_ptr, str
         raise PimcError(r, L.pimc_last_error(None).decode())
 
 
-def debug_fix_sum(terms, as_float=False):
-    """The exact sum parameter moves use, applied to a host array (test hook)."""
+def debug_fix_sum(terms, as_float=False, acc128=False):
+    """The exact sum parameter moves use, applied to a host array (test hook);
+    acc128: FP32 terms through the general form's 128-bit per-thread sum."""
     L = load()
     t = _f64(terms)
     out = np.zeros(1)
-    r = L.pimc_debug_fix_sum(_p(t), int(t.size), 1 if as_float else 0, _p(out))
+    mode = 2 if acc128 else (1 if as_float else 0)
+    r = L.pimc_debug_fix_sum(_p(t), int(t.size), mode, _p(out))
     if r != OK:
         raise PimcError(r, L.pimc_last_error(None).decode())
     return float(out[0])

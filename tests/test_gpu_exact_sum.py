@@ -19,18 +19,26 @@ def exact(terms):
     return float(Fraction(s, 1 << 64))
 
 
-@pytest.mark.parametrize("as_float", [False, True])
-def test_matches_exact_rational_sum(as_float):
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "fp32_acc128"])
+def test_matches_exact_rational_sum(mode):
+    """Also the 128-bit per-thread path of FP32 terms: below 2^36 a term is
+    shifted into one 128-bit integer, above it goes through the chunks; both
+    sides of that cut, subnormal and sub-2^-64 terms are in the mix."""
+    as_float, acc128 = mode != "fp64", mode == "fp32_acc128"
     rng = np.random.default_rng(3)
     for n, span in ((1, 10), (37, 4), (5000, 40), (100000, 58)):
         t = rng.standard_normal(n) * np.exp2(rng.integers(-span, span + 1, n).astype(float))
         if as_float:
             t = t.astype(np.float32).astype(np.float64)
-        got = pimc.debug_fix_sum(t, as_float=as_float)
+            if n > 1:
+                t[:4] = [2.0 ** 36, -(2.0 ** 36) + 2.0 ** 13, 2.0 ** -140, -(2.0 ** -70)]
+        got = pimc.debug_fix_sum(t, as_float=as_float, acc128=acc128)
         ref = exact(t)
         assert abs(got - ref) <= math.ulp(ref), (n, got, ref)
         perm = rng.permutation(n)
-        assert pimc.debug_fix_sum(t[perm], as_float=as_float) == got
+        assert pimc.debug_fix_sum(t[perm], as_float=as_float, acc128=acc128) == got
+        if as_float:  # the two FP32 paths give the same bits
+            assert pimc.debug_fix_sum(t, as_float=True, acc128=not acc128) == got
 
 
 def test_cancellation_is_exact():
@@ -38,6 +46,17 @@ def test_cancellation_is_exact():
     t = np.array([2.0 ** 60, 1.0, -(2.0 ** 60)] * 1000)
     assert pimc.debug_fix_sum(t) == 1000.0
     assert pimc.debug_fix_sum([2.0 ** -70, -(2.0 ** -70), 2.0 ** -65]) == 0.0  # below 2^-64: truncated
+
+
+@pytest.mark.parametrize("acc128", [False, True])
+def test_special_values_fp32(acc128):
+    inf, nan = float("inf"), float("nan")
+    f = lambda t: pimc.debug_fix_sum(t, as_float=True, acc128=acc128)
+    assert f([1.0, inf]) == inf and f([1.0, -inf]) == -inf
+    assert math.isnan(f([inf, -inf])) and math.isnan(f([0.5, nan]))
+    assert f([2.0 ** 62, -1.0]) == inf
+    big = np.full(1 << 20, -(2.0 ** 35))                      # the 128-bit path at its cut, 2^20 times
+    assert f(big) == -(2.0 ** 55)
 
 
 def test_special_values():
