@@ -504,33 +504,8 @@ def run_mixed(args):
     return out
 
 
-def _ess_bm(tr, secs, ess_geyer):
-    """Batch-means cross-check of the ESS: var(x) / se_bm^2 per parameter,
-    with about five effective samples a batch (5..30 batches) -- batches
-    shorter than the autocorrelation time would overstate the ESS."""
-    from paper_1103_4887_gb300 import diagnostics
-    n_batches = int(min(30, max(5, np.floor(np.min(ess_geyer) / 5.0))))
-    se = diagnostics.batch_means_se(tr, n_batches)
-    var = tr.var(axis=0, ddof=1)
-    ess = np.where(se > 0, var / np.maximum(se * se, 1e-300), float(tr.shape[0]))
-    return {"ess_batch_means": ess.tolist(), "batch_means_batches": n_batches,
-            "min_ess_batch_means_per_s": float(ess.min() / secs)}
-
-
-def run_ess(args, scale=1):
-    """Parameter ESS per second of sampling-phase device time (HH, M = 16384,
-    all 7 parameters free): checkerboard Metropolis and whole-path HMC, each
-    in FP32-mixed and FP64, on the same data.  Chains start at the true path
-    and parameters and adapt during a burn-in, so the figure measures mixing
-    in the posterior, not the approach to it.  scale multiplies the sampling
-    lengths: at scale 1 the slowest parameter gets only a few effective
-    samples (an indicative figure), at 20 some tens."""
+def _timer(st):
     import torch
-    from paper_1103_4887_gb300 import diagnostics, pimc, synth
-    M = 16384
-    prob = synth.hh_problem(M, data_seed=0, free="all")
-    out = {"M": M, "n_free": 7, "length_scale": scale}
-    st = torch.cuda.current_stream()
 
     def timed(fn):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -539,60 +514,164 @@ def run_ess(args, scale=1):
         e1.record(st)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e-3
+    return timed
 
-    for name, prec, burn, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, 4000, 100000 * scale),
-                                ("metropolis_fp64", pimc.FP64, 2000, 16000 * scale)):
-        s = pimc.Sampler.from_problem(prob, precision=prec)
-        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
-        s.set_path(prob.X_true)
-        s.set_stream(st.cuda_stream)
-        s.set_schedule(n_init=burn, n_skip=20, f_acc=0.4, alpha=0.5)
-        burn_secs = timed(lambda: s.sweep(burn, SEED, sync=False))
-        s.set_param_trace(n)
-        secs = timed(lambda: s.sweep(n, SEED, sync=False))
-        s.sync()
-        tr = s.param_trace()
-        ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
-        out[name] = {"sweeps": n, "seconds": secs, "burn_in_sweeps": burn, "burn_in_seconds": burn_secs,
-                     "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
-                     "median_ess_per_s": float(np.median(ess) / secs), **_ess_bm(tr, secs, ess),
-                     "mean_p": tr.mean(0).tolist()}
-        s.close()
 
-    # whole-path HMC: diagonal mass from burn-in variances, step tuned to ~70 %
-    for name, prec, n_traj in (("hmc_fp64", pimc.FP64, 2500 * scale),
-                               ("hmc_fp32mixed", pimc.FP32_MIXED, 10000 * scale)):
-        s = pimc.Sampler.from_problem(prob, precision=prec)
-        s.set_params(prob.p_true, prob.lo, prob.hi, prob.free)
-        s.set_path(prob.X_true)
-        s.set_stream(st.cuda_stream)
-        s.set_schedule(n_init=2000, n_skip=5, f_acc=0.4, alpha=0.5)
-        burn_secs = timed(lambda: s.sweep(4000, SEED, sync=False))
-        mean, var, J = s.moments()
-        inv_mass = np.where(np.isfinite(var) & (var > 0), var, 1e-12)
-        s.set_schedule(n_init=10 ** 9, n_skip=1)
-        eps, n_leap = 0.05, 20
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(12):
-            acc = s.hmc(10, n_leap, eps, inv_mass, seed=SEED) / 10.0
-            eps *= float(np.exp(1.5 * (acc - 0.7)))
-        e1.record(st)
-        torch.cuda.synchronize()
-        burn_secs += e0.elapsed_time(e1) * 1e-3
-        s.set_param_trace(n_traj)
-        acc_box = {}
-        secs = timed(lambda: acc_box.setdefault("n", s.hmc(n_traj, n_leap, eps, inv_mass, seed=SEED + 1)))
-        tr = s.param_trace()
-        ess = np.array([diagnostics.ess_geyer(tr[:, l]) for l in range(7)])
-        out[name] = {"trajectories": n_traj, "n_leap": n_leap, "eps": eps, "accept": acc_box["n"] / n_traj,
-                     "seconds": secs, "burn_in_seconds": burn_secs,
-                     "burn_in": "4000 Metropolis sweeps (mass from their variances) + 120 step-tuning trajectories",
-                     "ess": ess.tolist(), "min_ess_per_s": float(ess.min() / secs),
-                     "median_ess_per_s": float(np.median(ess) / secs), **_ess_bm(tr, secs, ess),
-                     "mean_p": tr.mean(0).tolist()}
-        s.close()
+def _ess_block(tr, secs, names, n_boot=100):
+    """Per parameter: multi-chain ESS with a bootstrap-over-chains SE, the
+    chain-means cross-check, split R-hat, mean and its MC standard error; the
+    minimum over parameters as ESS/s (tr: [K, n, P] parameter traces of K
+    chains, secs: device seconds of the sampling phase)."""
+    from paper_1103_4887_gb300 import diagnostics as dg
+    out = {"chains": int(tr.shape[0]), "steps_per_chain": int(tr.shape[1]), "seconds": secs, "params": {}}
+    ess_l = []
+    for j, nm in enumerate(names):
+        x = tr[:, :, j]
+        ess, se = dg.ess_with_se(x, n_boot=n_boot)
+        sd = float(x.std())
+        out["params"][nm] = {"ess": ess, "ess_se": se, "ess_chain_means": dg.ess_chain_means(x),
+                             "rhat": dg.split_rhat(x), "mean": float(x.mean()), "sd": sd,
+                             "mc_se": sd / np.sqrt(max(ess, 1.0))}
+        ess_l.append((ess, se, nm))
+    ess, se, nm = min(ess_l)
+    out.update({"min_ess": ess, "min_ess_se": se, "min_ess_param": nm, "min_ess_per_s": ess / secs,
+                "min_ess_per_s_se": se / secs, "max_rhat": max(v["rhat"] for v in out["params"].values())})
+    out["established"] = bool(out["max_rhat"] < 1.05 and ess >= 100.0)
     return out
+
+
+def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n_hmc=(1000, 200), n_leap=20,
+              names=None, seed=SEED):
+    """Parameter ESS per second of the four samplers on one posterior, from
+    independent chains that start in it.  A pilot of K batched FP32-mixed
+    Metropolis chains (from the data's initial path, adapting during its first
+    half) supplies each chain's starting state and steps, and the pooled
+    variances that serve as HMC's inverse mass.  Then, from those states and
+    with fresh seeds: K chains of batched checkerboard Metropolis in FP32-mixed
+    and in FP64 (n_metro sweeps each), and K_hmc chains of whole-path HMC in
+    FP32-mixed and FP64 (n_hmc trajectories of n_leap steps each, the step
+    tuned per chain to ~70 % acceptance first).  ESS/s divides by the device
+    time of the sampling phase; R-hat and the spread of chain means tell
+    whether the chains agree (ESS is meaningful only where they do)."""
+    import torch
+    from paper_1103_4887_gb300 import diagnostics as dg
+    from paper_1103_4887_gb300 import pimc
+    st = torch.cuda.current_stream()
+    timed = _timer(st)
+    free = np.flatnonzero(prob.free)
+    names = names or [f"p{j}" for j in free]
+    out = {"M": prob.M, "n_free": int(free.size), "K_metropolis": K, "K_hmc": K_hmc}
+
+    def make(prec, chain):
+        s = pimc.Sampler.from_problem(prob, precision=prec)
+        s.set_stream(st.cuda_stream)
+        s.set_chain(chain)
+        return s
+
+    # pilot
+    P = [make(pimc.FP32_MIXED, k) for k in range(K)]
+    for s in P:
+        s.set_schedule(n_init=pilot[0], n_skip=10, f_acc=0.4, alpha=0.5)
+        s.set_param_trace(pilot[1])
+    b = pimc.Batch(P)
+    out["pilot_seconds"] = timed(lambda: b.sweep(pilot[0] + pilot[1], seed + 100, sync=False))
+    b.close()
+    ptr = np.array([s.param_trace() for s in P])[:, :, free]
+    out["pilot"] = {"sweeps": pilot[0] + pilot[1], "adapting": pilot[0],
+                    "rhat_after_adaptation": {nm: dg.split_rhat(ptr[:, :, j]) for j, nm in enumerate(names)},
+                    "mean": dict(zip(names, ptr.mean(axis=(0, 1)).tolist()))}
+    starts = [s.state() for s in P]
+    steps = [s.steps() for s in P]
+    mv = np.array([s.moments()[:2] for s in P])  # [K, 2, D(M+1)+NP]
+    inv_mass = mv[:, 1].mean(axis=0) + mv[:, 0].var(axis=0)  # pooled variance
+    inv_mass = np.where(np.isfinite(inv_mass) & (inv_mass > 0), inv_mass, 1e-12)
+    for s in P:
+        s.close()
+
+    for key, prec, n in (("metropolis_fp32mixed", pimc.FP32_MIXED, n_metro[0]),
+                         ("metropolis_fp64", pimc.FP64, n_metro[1])):
+        S = [make(prec, k) for k in range(K)]
+        for s, (X, p), (sx, sp) in zip(S, starts, steps):
+            s.set_path(X)
+            s.set_params(p, prob.lo, prob.hi, prob.free)
+            s.set_steps(sx, sp)
+            s.set_schedule(n_init=10 ** 9, n_skip=10 ** 6)  # no statistics records, no adaptation
+            s.set_param_trace(n)
+        b = pimc.Batch(S)
+        chunk = max(n // 4, 1)
+        b.sweep(chunk, seed + 1)  # warm-up: captures the chunk's graph
+        secs = sum(timed(lambda: b.sweep(chunk, seed + 1, sync=False)) for _ in range(4))
+        b.close()
+        tr = np.array([s.param_trace() for s in S])[:, :, free]
+        out[key] = {"sweeps": 4 * chunk, **_ess_block(tr, secs, names)}
+        for s in S:
+            s.close()
+
+    for key, prec, n in (("hmc_fp32mixed", pimc.FP32_MIXED, n_hmc[0]), ("hmc_fp64", pimc.FP64, n_hmc[1])):
+        trs, secs, eps_l, acc_n = [], 0.0, [], 0
+        for k in range(K_hmc):
+            s = make(prec, 10000 + k)
+            X, p = starts[k]
+            s.set_path(X)
+            s.set_params(p, prob.lo, prob.hi, prob.free)
+            s.set_schedule(n_init=10 ** 9, n_skip=1)
+            eps = 0.05
+            for _ in range(10):
+                a = s.hmc(10, n_leap, eps, inv_mass, seed=seed + 2) / 10.0
+                eps *= float(np.exp(1.5 * (a - 0.7)))
+            s.set_param_trace(n)
+            box = {}
+            secs += timed(lambda: box.setdefault("n", s.hmc(n, n_leap, eps, inv_mass, seed=seed + 3)))
+            acc_n += box["n"]
+            eps_l.append(eps)
+            trs.append(s.param_trace()[:, free])
+            s.close()
+        out[key] = {"trajectories": n, "n_leap": n_leap, "eps_median": float(np.median(eps_l)),
+                    "accept": acc_n / (n * K_hmc), **_ess_block(np.array(trs), secs, names)}
+
+    # equal posterior accuracy: each sampler's means against plain FP64
+    # Metropolis, in pooled Monte Carlo standard errors
+    ref = out["metropolis_fp64"]["params"]
+    for key in ("metropolis_fp32mixed", "hmc_fp32mixed", "hmc_fp64"):
+        out[key]["mean_shift_vs_fp64_metropolis_in_se"] = {
+            nm: abs(v["mean"] - ref[nm]["mean"]) / np.hypot(v["mc_se"], ref[nm]["mc_se"])
+            for nm, v in out[key]["params"].items()}
+    base = out["metropolis_fp64"]["min_ess_per_s"]
+    for key in ("metropolis_fp32mixed", "hmc_fp32mixed", "hmc_fp64", "metropolis_fp64"):
+        out[key]["min_ess_per_s_vs_fp64_metropolis"] = out[key]["min_ess_per_s"] / base if base > 0 else None
+    return out
+
+
+def ess_default():
+    """The bounded ESS study of the default line (about half a minute): the
+    linear-Gaussian posterior at M = 200, and the HH problem at M = 2048 with
+    all 7 parameters free."""
+    from paper_1103_4887_gb300 import synth
+    lg = synth.lingauss_problem(200, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
+    hh = synth.hh_problem(2048, data_seed=0, free="all")
+    return {"lingauss_M200": ess_study(lg, K=64, K_hmc=32, pilot=(20000, 20000), n_metro=(40000, 32000),
+                                       n_hmc=(2000, 1000), n_leap=16, names=["b"]),
+            "hh_M2048_7free": ess_study(hh, K=64, K_hmc=16, pilot=(5000, 5000), n_metro=(20000, 2000),
+                                        n_hmc=(1000, 150), names=list(synth.HH_NAMES))}
+
+
+def run_ess(args):
+    """ESS study on the two posteriors: the linear-Gaussian test model (a
+    posterior every sampler mixes, at two path lengths) and the HH problem
+    with all 7 parameters free (M = 16384: the chains' R-hat shows whether they
+    agree within the run)."""
+    from paper_1103_4887_gb300 import synth
+    res = {}
+    for M in (200, 2000):
+        prob = synth.lingauss_problem(M, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
+        res[f"lingauss_M{M}"] = ess_study(prob, K=64, K_hmc=32, pilot=(20000, 20000), n_metro=(40000, 32000),
+                                          n_hmc=(2000, 1000), n_leap=16, names=["b"])
+        print(json.dumps({f"lingauss_M{M}": res[f"lingauss_M{M}"]}), flush=True)
+    prob = synth.hh_problem(16384, data_seed=0, free="all")
+    res["hh_M16384_7free"] = ess_study(prob, K=64, K_hmc=16, pilot=(20000, 20000), n_metro=(40000, 2000),
+                                       n_hmc=(1000, 150), names=list(synth.HH_NAMES))
+    print(json.dumps({"hh_M16384_7free": res["hh_M16384_7free"]}), flush=True)
+    return res
 
 
 def main():
@@ -622,9 +701,9 @@ def main():
                     help="FP32-mixed vs FP64 on the bench workload: Delta A error, accept-flip rate, "
                          "posterior-mean shift in MC standard errors")
     ap.add_argument("--ess", action="store_true",
-                    help="parameter ESS/s: FP32-mixed and FP64 Metropolis and whole-path HMC on the same data")
-    ap.add_argument("--ess-scale", type=int, default=20,
-                    help="sampling lengths of --ess relative to the short runs of the default line (which use 1)")
+                    help="parameter ESS/s of FP32-mixed and FP64 Metropolis and whole-path HMC from independent "
+                         "chains: linear-Gaussian posterior at M = 200 and 2000, HH with 7 free parameters at "
+                         "M = 16384")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -640,7 +719,7 @@ def main():
         run_sweep_M(args)
         return
     if args.ess:
-        print(json.dumps(run_ess(args, scale=args.ess_scale)), flush=True)
+        run_ess(args)
         return
     if args.mixed:
         print(json.dumps(run_mixed(args)), flush=True)
@@ -797,12 +876,7 @@ def main():
         except Exception as e:
             extras["mixed"] = {"error": repr(e)}
         try:
-            ess = run_ess(args)
-            keep = ("min_ess_per_s", "median_ess_per_s", "min_ess_batch_means_per_s", "seconds", "burn_in_seconds")
-            extras["ess"] = {k: ({kk: v[kk] for kk in keep if kk in v} if isinstance(v, dict) else v)
-                             for k, v in ess.items()}
-            extras["ess"]["note"] = ("short runs, indicative only: the slowest parameters' autocorrelation "
-                                     "times exceed these runs, which overstates ESS; bench.py --ess runs 20x longer")
+            extras["ess"] = ess_default()
         except Exception as e:
             extras["ess"] = {"error": repr(e)}
 

@@ -6,6 +6,7 @@ the unit counts (FP32 lanes 128 and SFU 16 per clock and SM)."""
 import importlib.util
 import os
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -63,3 +64,22 @@ def test_traffic_only_for_the_captured_kernel_sources(bench, monkeypatch):
     assert bench.traffic_of("general", 32768, 10) is None
     rec[("resident", 32768)]["src"] = "0" * 16
     assert bench.traffic_of("resident", 32768, 10) is None
+
+
+def test_ess_block_flags_agreement_and_length(bench):
+    rng = np.random.default_rng(0)
+    K, n, phi = 32, 2000, 0.5
+    x = np.empty((K, n, 2))
+    x[:, 0] = rng.standard_normal((K, 2)) / np.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + rng.standard_normal((K, 2))
+    blk = bench._ess_block(x, 2.0, ["a", "b"], n_boot=20)
+    assert blk["established"] and blk["max_rhat"] < 1.05
+    assert blk["min_ess"] == min(v["ess"] for v in blk["params"].values())
+    assert blk["min_ess_per_s"] == pytest.approx(blk["min_ess"] / 2.0)
+    # AR(1) with phi = 1/2: tau = 3
+    assert abs(blk["min_ess"] - K * n / 3) < 0.15 * K * n / 3
+    y = x.copy()
+    y[: K // 2, :, 1] += 5.0  # half the chains elsewhere in one parameter
+    blk2 = bench._ess_block(y, 2.0, ["a", "b"], n_boot=20)
+    assert not blk2["established"] and blk2["params"]["b"]["rhat"] > 1.5

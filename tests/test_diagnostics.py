@@ -77,3 +77,43 @@ def test_replica_moment_merge_over_gloo_ranks():
     assert all(p.exitcode == 0 for p in ps)
     dm, dv = q.get(timeout=10)
     assert dm < 1e-12 and dv < 1e-12
+
+
+def _ar1_chains(K, n, phi, seed):
+    rng = np.random.default_rng(seed)
+    x = np.empty((K, n))
+    x[:, 0] = rng.standard_normal(K) / np.sqrt(1 - phi * phi)  # stationary start
+    e = rng.standard_normal((K, n))
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + e[:, t]
+    return x
+
+
+def test_multichain_ess_matches_ar1_closed_form():
+    # AR(1): integrated autocorrelation time (1 + phi) / (1 - phi)
+    for phi in (0.0, 0.5, 0.9):
+        x = _ar1_chains(32, 4000, phi, seed=int(phi * 10))
+        tau = (1 + phi) / (1 - phi)
+        ess, se = dg.ess_with_se(x, n_boot=50)
+        assert abs(ess - x.size / tau) < 4 * se + 0.05 * x.size / tau, (phi, ess, x.size / tau, se)
+        assert dg.split_rhat(x) < 1.02
+        # the chain-means estimate agrees within its own spread (relative SE ~ sqrt(2/(K-1)))
+        cm = dg.ess_chain_means(x)
+        assert abs(np.log(cm / (x.size / tau))) < 3 * np.sqrt(2 / 31), (phi, cm)
+
+
+def test_multichain_ess_single_chain_equals_geyer():
+    x = _ar1_chains(1, 5000, 0.7, seed=3)
+    # one chain: B = 0 and var+ = (n-1)/n W, the pooled estimator is Geyer's up to that factor
+    a = dg.ess_multichain(x)
+    b = dg.ess_geyer(x[0])
+    assert abs(a - b) / b < 0.01
+
+
+def test_split_rhat_flags_chains_that_disagree():
+    x = _ar1_chains(8, 2000, 0.5, seed=4)
+    x[:4] += 3.0  # half the chains in another place
+    assert dg.split_rhat(x) > 1.5
+    y = _ar1_chains(8, 2000, 0.5, seed=5)
+    y += np.linspace(0, 5, 2000)  # a drift within every chain
+    assert dg.split_rhat(y) > 1.1
