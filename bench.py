@@ -362,6 +362,7 @@ def run_batch(args):
     import torch
     from paper_1103_4887_gb300 import pimc, synth
     rng = np.random.default_rng(2024)
+    st = torch.cuda.current_stream()  # the batch launches on its first handle's stream
     n_sets, per_set = 64, 8
     Ms = rng.integers(2048, 65537, size=n_sets)
     samplers = []
@@ -371,23 +372,28 @@ def run_batch(args):
         prob = synth.hh_problem(int(Ms[d]), data_seed=100 + d, free=("gNa", "gK", "gL"), p_true=q)
         for k in range(per_set):
             s = pimc.Sampler.from_problem(prob, precision=pimc.FP32_MIXED)
+            s.set_stream(st.cuda_stream)
             s.set_chain(k)
             s.set_schedule(n_init=10 ** 6, n_skip=20, f_acc=0.4, alpha=0.5)
             samplers.append(s)
     b = pimc.Batch(samplers)
-    nt, k = b.autotune(4, SEED)
+    nt, k, g = b.autotune(4, SEED)
     steps = max(args.steps // 30, 20)
     b.sweep(steps, SEED)  # warm-up: also captures the graph of a `steps`-sweep block
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b.sweep(steps, SEED)
-    el = time.perf_counter() - t0
+    el = _timer(st)(lambda: b.sweep(steps, SEED, sync=False))
     sites = int(sum(int(m) + 1 for m in Ms)) * per_set
-    n_ctas, _ = b.info()
+    maps = int(sum(maps_per_sweep(int(m), 3) for m in Ms)) * per_set
+    n_ctas, _, n_split = b.info()
+    peaks, _ = load_peaks()
+    fr = roofline_fracs(maps * steps, el, torch.cuda.get_device_properties(0).multi_processor_count,
+                        float(peaks.get("sm_max_mhz", 2070.0)))
     res = {"mode": "batch", "chains": n_sets * per_set, "data_sets": n_sets, "sites_per_sweep": sites,
            "sweeps": steps, "seconds": el, "site_updates_per_s": sites * steps / el,
            "ms_per_sweep_all_chains": 1e3 * el / steps, "tuning": {"threads_per_cta": nt,
-           "ctas_per_sm": k, "ctas": n_ctas}, "precision": "fp32mixed"}
+           "ctas_per_sm": k, "ctas_per_long_chain": g, "chains_split": n_split, "ctas": n_ctas}, "precision": "fp32mixed",
+           "rk4_maps_per_s": maps * steps / el, "frac_recount": fr["frac_recount"],
+           "frac_survey_count": fr["frac_survey_count"]}
     b.close()
     for s in samplers:
         s.close()

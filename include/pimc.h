@@ -289,10 +289,10 @@ int pimc_set_sweep_form(pimc_t h, int form);
 typedef struct pimc_batch_s* pimc_batch_t;
 
 /* Group n handles (same model, precision and device; data and parameters set)
- * into one launch.  Every CTA owns whole chains and runs them one after
- * another with CTA-local synchronisation (no grid barrier); chains are
- * assigned to CTAs longest-first onto the least loaded CTA, with a chain's
- * cost (M + 1)(1 + free parameters).  Each chain keeps its own handle: state,
+ * into one launch.  Every CTA runs whole chains one after another with
+ * CTA-local synchronisation, or tiles of long chains shared with other CTAs
+ * (pimc_batch_set_tuning); chains are assigned to CTAs longest-first onto the
+ * least loaded CTA(s), with a chain's cost (M + 1)(1 + free parameters).  Each chain keeps its own handle: state,
  * schedule, statistics, trace and checkpoints are read and set through it.
  * Handles must have no work in flight and must not be used while a batch
  * sweep runs (call pimc_batch_sync first).  A chain runs exactly the sweeps it
@@ -307,14 +307,25 @@ const char* pimc_batch_last_error(pimc_batch_t b);
  * or seed change). */
 int pimc_batch_sweep(pimc_batch_t b, int64_t n_sweeps, uint64_t seed);
 int pimc_batch_sync(pimc_batch_t b);
-/* Tile shape: threads per CTA (128 or 256) and resident CTAs per SM (0 = as
- * many as fit), i.e. how many chains share a CTA. */
-int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm);
-int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta);
+/* Tile shape (the block decomposition of Sec. 4.3 for many chains): threads
+ * per CTA (128 or 256), resident CTAs per SM (0 = as many as fit), i.e. how
+ * many chains share a CTA, and ctas_per_chain (1..64): a chain costing more
+ * than a CTA's mean load is cut into up to that many tiles of even length (at
+ * least 2 * threads_per_cta sites each), run together by as many CTAs of the
+ * launch, which synchronise on the chain's own barrier word and exact-sum
+ * slots with bounded waits (the launch is then cooperative); 1 keeps every
+ * chain whole.  A chain's results do not depend on the tile shape.
+ * PIMC_ERR_ARG for values out of range. */
+int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm, int ctas_per_chain);
+/* The current plan: CTAs of a launch, threads per CTA, chains split over
+ * several CTAs (any output may be NULL). */
+int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta, int* n_split);
 /* Time trial_sweeps real sweeps (they advance every chain: run this during
- * burn-in) for each tile shape and keep the fastest; the choice is cached per
+ * burn-in) for each tile shape -- threads per CTA x CTAs per SM x CTAs per
+ * long chain (1, 2, 4) -- and keep the fastest; the choice is cached per
  * process for batches of the same model, precision, size and chain count. */
-int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm);
+int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm,
+                        int* ctas_per_chain);
 
 /* ---- checkpoint / resume ------------------------------------------------------ */
 /* Binary file with a version and a CRC: sizes, settings, path, p, steps,
@@ -326,6 +337,19 @@ int pimc_checkpoint_load(pimc_t h, const char* path);
 /* ---- test hooks ---------------------------------------------------------------- */
 /* Bounded-wait limit of the grid barrier in nanoseconds (default 2e9). */
 int pimc_set_wait_limit(pimc_t h, int64_t ns);
+/* Checked builds only (libpimc_check.so: the same sources compiled with
+ * PIMC_CHECK, in which the sweep kernels count site visits and check site
+ * indices; the race and bounds check of the checkerboard, Sec. 4.1 and
+ * Sec. 4.3).  Since the last reset: even[n], odd[n] (M+1 each, host,
+ * caller-owned): visits of site n in the even and the odd site phases;
+ * param[n] (M+1): the parameter moves' cache writes of site n; *moves: the
+ * parameter moves executed (in-box proposals); *status: the handle's sticky
+ * status, bit 2 set when a site index outside [0, M] was met (that access
+ * skipped, nothing trapped).  Any output may be NULL; reset != 0 clears the
+ * counts and bit 2 afterwards.  Synchronous.  PIMC_ERR_STATE in an unchecked
+ * build. */
+int pimc_debug_check_counts(pimc_t h, uint32_t* even, uint32_t* odd, uint32_t* param, uint64_t* moves,
+                            int* status, int reset);
 /* Make CTA `cta` skip its barrier arrivals in later sweeps (-1: off), so the
  * other CTAs' bounded waits expire and pimc_sync reports PIMC_ERR_TIMEOUT. */
 int pimc_debug_skip_arrive(pimc_t h, int cta);

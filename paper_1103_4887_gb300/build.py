@@ -1,7 +1,10 @@
 """In-tree build of the CUDA sampler library (sm_103a) and the input generator.
 
 ``build()`` compiles each translation unit of ``csrc/`` with nvcc in parallel
-and links ``_build/libpimc.so``; nothing is installed outside the tree.
+and links ``_build/libpimc.so``, and the checked variant
+``_build/libpimc_check.so`` (the sweep kernels compiled with PIMC_CHECK: site
+visit counters and index checks, for tests); nothing is installed outside the
+tree.
 """
 from __future__ import annotations
 
@@ -14,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpimc.so")
+LIB_CHECK = os.path.join(BUILD, "libpimc_check.so")
+CHECKED_SOURCES = ["sweep.cu"]  # the translation units that differ under PIMC_CHECK
 ROOT = os.path.dirname(HERE)
 
 CU_SOURCES = ["sweep.cu", "ops.cu", "runtime.cu", "noalloc.cu", "hmc.cu"]
@@ -45,6 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pimc.h")]
     jobs = []
     objs = []
+    objs_check = []
     for src in CU_SOURCES:
         sp = os.path.join(CSRC, src)
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -54,6 +60,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
+        if src in CHECKED_SOURCES:
+            objc = os.path.join(BUILD, src.replace(".cu", "_check.o"))
+            objs_check.append(objc)
+            if force or _stale(objc, [sp] + hdrs):
+                jobs.append([nvcc] + _flags() + ["-DPIMC_CHECK", "-c", sp, "-o", objc])
+        else:
+            objs_check.append(obj)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,10 +81,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for l in logs:
             print(l)
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
+    for lib, ob in ((LIB, objs), (LIB_CHECK, objs_check)):
+        if force or jobs or not os.path.exists(lib):
+            tmp = lib + f".{os.getpid()}.tmp"
+            run([nvcc] + ARCH + ["-shared", "-o", tmp] + ob + ["-lcudart"])
+            os.replace(tmp, lib)
     return LIB
 
 

@@ -27,11 +27,12 @@ struct DevState {
     unsigned accp_win[8];
     unsigned long long site_acc[2], site_prop[2], par_acc[8], par_prop[8], nonfinite;
     long long tr_n;  // parameter vectors written to the trace ring so far
-    int status;   // sticky error bits (kStatusTimeout)
+    int status;   // sticky error bits (kStatusTimeout, kStatusBounds)
     int abort;    // set by a CTA whose bounded wait expired; all CTAs leave
 };
 
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusBounds = 2;  // checked builds: a site index outside [0, M] was met (access skipped)
 
 // Everything a kernel needs, passed by value.
 struct Ctx {
@@ -68,7 +69,14 @@ struct Ctx {
     int64_t wait_ns;
     int skip_cta;
     int64_t tile;                 // sites per CTA in the sweep kernel
+    unsigned* chk;                // [3][ldx] site visits (even phase, odd phase, parameter-move cache
+                                  // writes), then a u64 count of executed parameter moves: counted by
+                                  // builds compiled with PIMC_CHECK only
 };
+
+// 1 in a build compiled with PIMC_CHECK (the sweep kernels count site visits
+// and check site indices), 0 otherwise.
+int checked_build();
 
 // Device-side scalars of one HMC trajectory.
 struct HmcScalars {
@@ -107,10 +115,18 @@ cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, in
 int sweep_max_grid(int model, int prec, int device, int resident);
 // whether a launch of `grid` CTAs with tiles of `tile` sites takes the resident form
 bool resident_fits(int prec, int64_t tile, int grid);
-// Many whole chains in one launch (nt threads per CTA: 128 or 256): CTA b runs
-// chains[order[first[b] .. first[b+1])] one after another.
-cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first, const int* order,
-                               int n_ctas, int64_t n_sweeps, uint64_t seed, cudaStream_t s);
+// One piece of work of a batched launch: chain `chain` alone (size 1), or its
+// tile `rank` of `size` equal tiles, which `size` CTAs of the launch run
+// together.
+struct BatchItem {
+    int chain, rank, size, pad;
+};
+// Many chains in one launch (nt threads per CTA: 128 or 256): CTA b runs
+// items[first[b] .. first[b+1]) one after another.  cooperative: some chain
+// is split over several CTAs (the launch guarantees they are co-resident).
+cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first,
+                               const BatchItem* items, int n_ctas, int64_t n_sweeps, uint64_t seed, bool cooperative,
+                               cudaStream_t s);
 int batch_ctas_per_sm(int model, int prec, int nt);
 cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s);
 cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s);

@@ -41,6 +41,7 @@ struct pimc_handle_s {
     bool resident = false;                // the sweep takes the resident form (one site a thread)
     int form = PIMC_FORM_AUTO;            // forms the sweep may take
     unsigned* ticket = nullptr;
+    unsigned* chk = nullptr;          // site-visit counters of checked builds
     double* red = nullptr;
     double* pdraw = nullptr;          // parameter draws of a resident launch
     double *S1 = nullptr, *S2 = nullptr, *shift = nullptr;
@@ -121,6 +122,7 @@ Ctx make_ctx(pimc_t h)
     c.fbeta = h->fbeta; c.f_acc = h->f_acc; c.alpha = h->alpha;
     c.chain = h->chain; c.wait_ns = h->wait_ns; c.skip_cta = h->skip_cta;
     c.tile = h->tile;
+    c.chk = h->chk;
     return c;
 }
 
@@ -230,7 +232,7 @@ int check_finite(const double* v, int64_t n)
 void free_all(pimc_t h)
 {
     void* bufs[] = {h->X, h->F[0], h->F[1], h->y, h->I, h->sig, h->acc_win, h->st, h->partials, h->bar, h->flags,
-                    h->ticket, h->red, h->pdraw, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
+                    h->ticket, h->chk, h->red, h->pdraw, h->S1, h->S2, h->shift, h->hist, h->h_comp, h->h_lo, h->h_hi,
                     h->dense, h->small, h->y64, h->I64, h->trace, h->R1, h->R2, h->hmc.hs, h->hmc.Q, h->hmc.P,
                     h->hmc.Q2, h->hmc.EM, h->hmc.invm};
     for (void* b : bufs)
@@ -308,6 +310,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
         {(void**)&h->bar, sizeof(unsigned) * 4},
         {(void**)&h->flags, sizeof(unsigned long long) * 2 * kMaxGrid},
         {(void**)&h->ticket, sizeof(unsigned) * 4},
+        {(void**)&h->chk, sizeof(unsigned) * (3 * h->ldx + 2)},
         {(void**)&h->red, sizeof(double) * 2 * kRedStride * kMaxGrid},
         {(void**)&h->pdraw, sizeof(double) * 2 * kMaxParams * kDrawChunk},
         {(void**)&h->S1, sizeof(double) * nc},
@@ -334,6 +337,7 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
     cudaMemset(h->bar, 0, sizeof(unsigned) * 4);
     cudaMemset(h->flags, 0, sizeof(unsigned long long) * 2 * kMaxGrid);
     cudaMemset(h->ticket, 0, sizeof(unsigned) * 4);
+    cudaMemset(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2));
     cudaMemset(h->X, 0, sizeof(double) * D * h->ldx);
     cudaMemset(h->F[0], 0, sizeof(double) * D * h->ldf);
     cudaMemset(h->F[1], 0, sizeof(double) * D * h->ldf);
@@ -1001,6 +1005,28 @@ int pimc_debug_lane_maps(const double* X, const double* I_inj, const double* p, 
     return PIMC_OK;
 }
 
+int pimc_debug_check_counts(pimc_t h, uint32_t* even, uint32_t* odd, uint32_t* param, uint64_t* moves, int* status,
+                            int reset)
+{
+    if (!h) return PIMC_ERR_ARG;
+    if (!checked_build()) return fail(h, PIMC_ERR_STATE, "not a checked build (compile with PIMC_CHECK)");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int64_t n1 = h->M + 1;
+    uint32_t* outs[3] = {even, odd, param};
+    for (int k = 0; k < 3; ++k)
+        if (outs[k]) CK(h, cudaMemcpy(outs[k], h->chk + k * h->ldx, sizeof(uint32_t) * n1, cudaMemcpyDeviceToHost));
+    if (moves) CK(h, cudaMemcpy(moves, h->chk + 3 * h->ldx, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    int r = pull_state(h);
+    if (r != PIMC_OK) return r;
+    if (status) *status = h->hs.status;
+    if (reset) {
+        CK(h, cudaMemset(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2)));
+        h->hs.status &= ~kStatusBounds;
+        if ((r = push_state(h)) != PIMC_OK) return r;
+    }
+    return PIMC_OK;
+}
+
 int pimc_debug_skip_arrive(pimc_t h, int cta)
 {
     if (!h) return PIMC_ERR_ARG;
@@ -1236,8 +1262,10 @@ struct pimc_batch_s {
     cudaStream_t stream = nullptr;
     Ctx* d_ctx = nullptr;
     int* d_first = nullptr;
-    int* d_order = nullptr;
+    BatchItem* d_items = nullptr;
     int n_ctas = 0, nt = 256, ctas_per_sm = 0;
+    int split = 1;          // most CTAs one chain may be split over
+    int n_split = 0;        // chains split over several CTAs in the current plan
     std::vector<unsigned> versions;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_sweeps = -1;
@@ -1276,17 +1304,25 @@ double chain_cost(pimc_t h)
     return (double)(h->M + 1) * (double)(1 + nf);
 }
 
-// Contexts of all chains and a longest-processing-time-first assignment of
-// whole chains to CTAs (each chain to the currently least loaded CTA).
+// Contexts of all chains and their assignment to CTAs, longest first.  With
+// split > 1, a chain costing more than the mean load of a CTA is cut into up
+// to `split` tiles (at least 2 nt sites each), which go to that many of the
+// currently least loaded CTAs; every other chain goes whole to the least
+// loaded CTA.  Each CTA's items are appended in one global order (decreasing
+// cost), so the CTAs sharing a split chain always reach it without a cycle of
+// waits.
 int batch_build(pimc_batch_t b)
 {
     const int n = (int)b->hs.size();
-    int dev = b->hs[0]->device, sms = b->hs[0]->num_sms;
-    (void)dev;
+    const int sms = b->hs[0]->num_sms;
     int occ = batch_ctas_per_sm(b->model, b->prec, b->nt);
     if (occ < 1) return bfail(b, PIMC_ERR_CUDA, "batched kernel cannot be resident (nt = %d)", b->nt);
     int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
-    b->n_ctas = std::max(1, std::min(n, per_sm * sms));
+    std::vector<double> cost(n);
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) total += (cost[i] = chain_cost(b->hs[i]));
+    // enough CTAs for every chain, or for every tile when chains are split
+    b->n_ctas = std::max(1, std::min(b->split > 1 ? per_sm * sms : n, per_sm * sms));
     std::vector<Ctx> ctx(n);
     std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) {
@@ -1294,36 +1330,48 @@ int batch_build(pimc_batch_t b)
         idx[i] = i;
         b->versions[i] = b->hs[i]->ctx_version;
     }
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](int a, int c) { return chain_cost(b->hs[a]) > chain_cost(b->hs[c]); });
-    typedef std::pair<double, int> Load;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
-    for (int k = 0; k < b->n_ctas; ++k) pq.push(Load(0.0, k));
-    std::vector<std::vector<int>> per(b->n_ctas);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    const double target = total / b->n_ctas;
+    std::vector<double> load(b->n_ctas, 0.0);
+    std::vector<std::vector<BatchItem>> per(b->n_ctas);
+    std::vector<int> by_load(b->n_ctas);
+    b->n_split = 0;
     for (int i : idx) {
-        Load l = pq.top();
-        pq.pop();
-        per[l.second].push_back(i);
-        l.first += chain_cost(b->hs[i]);
-        pq.push(l);
+        int g = 1;
+        if (b->split > 1 && cost[i] > target) {
+            const int64_t max_tiles = std::max<int64_t>(1, (b->hs[i]->M + 1) / (2 * b->nt));
+            g = (int)std::min<int64_t>({(int64_t)b->split, (int64_t)std::ceil(cost[i] / target), max_tiles,
+                                        (int64_t)b->n_ctas});
+            g = std::max(g, 1);
+        }
+        for (int k = 0; k < b->n_ctas; ++k) by_load[k] = k;
+        std::partial_sort(by_load.begin(), by_load.begin() + g, by_load.end(),
+                          [&](int a, int c) { return load[a] < load[c] || (load[a] == load[c] && a < c); });
+        std::sort(by_load.begin(), by_load.begin() + g);
+        for (int r = 0; r < g; ++r) {
+            per[by_load[r]].push_back(BatchItem{i, r, g, 0});
+            load[by_load[r]] += cost[i] / g;
+        }
+        if (g > 1) b->n_split++;
     }
-    std::vector<int> first(b->n_ctas + 1, 0), order;
-    order.reserve(n);
+    std::vector<int> first(b->n_ctas + 1, 0);
+    std::vector<BatchItem> items;
+    items.reserve(n + 64);
     for (int k = 0; k < b->n_ctas; ++k) {
-        first[k] = (int)order.size();
-        for (int i : per[k]) order.push_back(i);
+        first[k] = (int)items.size();
+        for (const BatchItem& it : per[k]) items.push_back(it);
     }
-    first[b->n_ctas] = (int)order.size();
+    first[b->n_ctas] = (int)items.size();
     if (b->d_ctx) cudaFree(b->d_ctx);
     if (b->d_first) cudaFree(b->d_first);
-    if (b->d_order) cudaFree(b->d_order);
-    b->d_ctx = nullptr; b->d_first = nullptr; b->d_order = nullptr;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_ctx = nullptr; b->d_first = nullptr; b->d_items = nullptr;
     BCK(b, cudaMalloc(&b->d_ctx, sizeof(Ctx) * n));
     BCK(b, cudaMalloc(&b->d_first, sizeof(int) * (b->n_ctas + 1)));
-    BCK(b, cudaMalloc(&b->d_order, sizeof(int) * n));
+    BCK(b, cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
     BCK(b, cudaMemcpy(b->d_ctx, ctx.data(), sizeof(Ctx) * n, cudaMemcpyHostToDevice));
     BCK(b, cudaMemcpy(b->d_first, first.data(), sizeof(int) * (b->n_ctas + 1), cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -1332,9 +1380,18 @@ int batch_build(pimc_batch_t b)
     return PIMC_OK;
 }
 
-std::map<std::pair<int, int>, std::pair<int, int>>& tune_cache()
+cudaError_t batch_launch(pimc_batch_t b, int64_t n_sweeps, uint64_t seed)
 {
-    static std::map<std::pair<int, int>, std::pair<int, int>> m;
+    return launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_items, b->n_ctas, n_sweeps, seed,
+                              b->n_split > 0, b->stream);
+}
+
+struct Tuning {
+    int nt, ctas_per_sm, split;
+};
+std::map<std::pair<int, int>, Tuning>& tune_cache()
+{
+    static std::map<std::pair<int, int>, Tuning> m;
     return m;
 }
 
@@ -1373,7 +1430,11 @@ int pimc_batch_create(pimc_batch_t* out, const pimc_t* handles, int n)
     b->stream = handles[0]->stream;
     b->versions.assign(n, ~0u);
     auto it = tune_cache().find(std::make_pair(tune_key_sites(b), n));
-    if (it != tune_cache().end()) { b->nt = it->second.first; b->ctas_per_sm = it->second.second; }
+    if (it != tune_cache().end()) {
+        b->nt = it->second.nt;
+        b->ctas_per_sm = it->second.ctas_per_sm;
+        b->split = it->second.split;
+    }
     int r = batch_build(b);
     if (r != PIMC_OK) {
         g_create_error = b->err;
@@ -1391,29 +1452,32 @@ int pimc_batch_destroy(pimc_batch_t b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->d_ctx) cudaFree(b->d_ctx);
     if (b->d_first) cudaFree(b->d_first);
-    if (b->d_order) cudaFree(b->d_order);
+    if (b->d_items) cudaFree(b->d_items);
     delete b;
     return PIMC_OK;
 }
 
 const char* pimc_batch_last_error(pimc_batch_t b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
-int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm)
+int pimc_batch_set_tuning(pimc_batch_t b, int threads_per_cta, int ctas_per_sm, int ctas_per_chain)
 {
     if (!b) return PIMC_ERR_ARG;
     if (threads_per_cta != 128 && threads_per_cta != 256) return bfail(b, PIMC_ERR_ARG, "threads_per_cta must be 128 or 256");
     if (ctas_per_sm < 0) return bfail(b, PIMC_ERR_ARG, "ctas_per_sm must be >= 0");
+    if (ctas_per_chain < 1 || ctas_per_chain > 64) return bfail(b, PIMC_ERR_ARG, "ctas_per_chain must be in [1, 64]");
     BCK(b, cudaStreamSynchronize(b->stream));
     b->nt = threads_per_cta;
     b->ctas_per_sm = ctas_per_sm;
+    b->split = ctas_per_chain;
     return batch_build(b);
 }
 
-int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta)
+int pimc_batch_info(pimc_batch_t b, int* n_ctas, int* threads_per_cta, int* n_split)
 {
     if (!b) return PIMC_ERR_ARG;
     if (n_ctas) *n_ctas = b->n_ctas;
     if (threads_per_cta) *threads_per_cta = b->nt;
+    if (n_split) *n_split = b->n_split;
     return PIMC_OK;
 }
 
@@ -1442,8 +1506,7 @@ int pimc_batch_sweep(pimc_batch_t b, int64_t n_sweeps, uint64_t seed)
             BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
             for (int64_t done = 0; done < n_sweeps && e == cudaSuccess; done += chunk)
-                e = launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
-                                       std::min<int64_t>(chunk, n_sweeps - done), seed, b->stream);
+                e = batch_launch(b, std::min<int64_t>(chunk, n_sweeps - done), seed);
             cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
             if (e == cudaSuccess) e = e2;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
@@ -1457,8 +1520,7 @@ int pimc_batch_sweep(pimc_batch_t b, int64_t n_sweeps, uint64_t seed)
         BCK(b, cudaGraphLaunch(b->exec, b->stream));
     } else {
         for (int64_t done = 0; done < n_sweeps; done += chunk)
-            BCK(b, launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
-                                      std::min<int64_t>(chunk, n_sweeps - done), seed, b->stream));
+            BCK(b, batch_launch(b, std::min<int64_t>(chunk, n_sweeps - done), seed));
     }
     return PIMC_OK;
 }
@@ -1470,7 +1532,8 @@ int pimc_batch_sync(pimc_batch_t b)
     return PIMC_OK;
 }
 
-int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm)
+int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int* threads_per_cta, int* ctas_per_sm,
+                        int* ctas_per_chain)
 {
     if (!b) return PIMC_ERR_ARG;
     if (trial_sweeps < 1) return bfail(b, PIMC_ERR_ARG, "trial_sweeps must be >= 1");
@@ -1479,32 +1542,41 @@ int pimc_batch_autotune(pimc_batch_t b, int64_t trial_sweeps, uint64_t seed, int
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nt = b->nt, best_k = b->ctas_per_sm;
+    Tuning best_t{b->nt, b->ctas_per_sm, b->split};
     const int nts[2] = {128, 256};
+    const int splits[3] = {1, 2, 4};
     for (int ni = 0; ni < 2; ++ni) {
         const int occ = batch_ctas_per_sm(b->model, b->prec, nts[ni]);
         for (int k = 1; k <= occ; k *= 2) {
-            b->nt = nts[ni];
-            b->ctas_per_sm = k;
-            int r = batch_build(b);
-            if (r != PIMC_OK) return r;
-            BCK(b, cudaEventRecord(e0, b->stream));
-            BCK(b, launch_batch_sweep(b->model, b->prec, b->nt, b->d_ctx, b->d_first, b->d_order, b->n_ctas,
-                                      trial_sweeps, seed, b->stream));
-            BCK(b, cudaEventRecord(e1, b->stream));
-            BCK(b, cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            BCK(b, cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_nt = nts[ni]; best_k = k; }
+            for (int si = 0; si < 3; ++si) {
+                b->nt = nts[ni];
+                b->ctas_per_sm = k;
+                b->split = splits[si];
+                int r = batch_build(b);
+                if (r != PIMC_OK) return r;
+                if (splits[si] > 1 && b->n_split == 0) continue;  // nothing to split: same as split 1
+                BCK(b, cudaEventRecord(e0, b->stream));
+                BCK(b, batch_launch(b, trial_sweeps, seed));
+                BCK(b, cudaEventRecord(e1, b->stream));
+                BCK(b, cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_t = Tuning{nts[ni], k, splits[si]};
+                }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->nt = best_nt;
-    b->ctas_per_sm = best_k;
-    tune_cache()[std::make_pair(tune_key_sites(b), (int)b->hs.size())] = std::make_pair(best_nt, best_k);
-    if (threads_per_cta) *threads_per_cta = best_nt;
-    if (ctas_per_sm) *ctas_per_sm = best_k;
+    b->nt = best_t.nt;
+    b->ctas_per_sm = best_t.ctas_per_sm;
+    b->split = best_t.split;
+    tune_cache()[std::make_pair(tune_key_sites(b), (int)b->hs.size())] = best_t;
+    if (threads_per_cta) *threads_per_cta = best_t.nt;
+    if (ctas_per_sm) *ctas_per_sm = best_t.ctas_per_sm;
+    if (ctas_per_chain) *ctas_per_chain = best_t.split;
     return batch_build(b);
 }
 

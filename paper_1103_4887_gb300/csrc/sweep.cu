@@ -93,19 +93,20 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Grid-wide barrier on one 32-bit word: every CTA adds 1, except CTA 0 which
-// adds 2^31 - (G - 1), so the word's top bit flips exactly when all G CTAs
-// have arrived and its low bits return to their old value.  Arrival is a
-// release (fence, then a relaxed add that returns nothing); each CTA knows the
-// top bit before the barrier (`phase`, read at launch start and toggled at
-// every barrier) and polls with acquire loads until it flips.  The wait is
-// bounded by c.wait_ns: on expiry the CTA flags kStatusTimeout and the abort
-// word, and every CTA leaves the launch at its next wait.
-__device__ __forceinline__ void grid_arrive(const Ctx& c)
+// Barrier of the G CTAs that share a chain (the whole grid of a chain's own
+// launch, or a group of a batched launch) on the chain's 32-bit word: every
+// CTA adds 1, except rank 0 which adds 2^31 - (G - 1), so the word's top bit
+// flips exactly when all G CTAs have arrived and its low bits return to their
+// old value.  Arrival is a release (fence, then a relaxed add that returns
+// nothing); each CTA knows the top bit before the barrier (`phase`, read at
+// the chain's start and toggled at every barrier) and polls with acquire loads
+// until it flips.  The wait is bounded by c.wait_ns: on expiry the CTA flags
+// kStatusTimeout and the abort word, and every CTA leaves at its next wait.
+__device__ __forceinline__ void grid_arrive(const Ctx& c, int rank, int size)
 {
-    const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (gridDim.x - 1u)) : 1u;
+    const unsigned add = (rank == 0) ? (0x80000000u - (unsigned)(size - 1)) : 1u;
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    if ((int)blockIdx.x != c.skip_cta)
+    if (rank != c.skip_cta)
         asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(c.bar), "r"(add) : "memory");
 }
 
@@ -125,19 +126,19 @@ __device__ __forceinline__ bool grid_wait(const Ctx& c, unsigned phase)
 }
 
 // One thread: arrive, wait, and toggle the tracked top bit.
-__device__ __forceinline__ bool grid_sync_one(const Ctx& c, unsigned* phase)
+__device__ __forceinline__ bool grid_sync_one(const Ctx& c, unsigned* phase, int rank, int size)
 {
-    grid_arrive(c);
+    grid_arrive(c, rank, size);
     const bool ok = grid_wait(c, *phase);
     *phase ^= 1u;
     return ok;
 }
 
 // Whole-CTA form.  Returns false when leaving.
-__device__ bool grid_barrier(const Ctx& c, int* s_abort, unsigned* phase)
+__device__ bool grid_barrier(const Ctx& c, int* s_abort, unsigned* phase, int rank, int size)
 {
     __syncthreads();
-    if (threadIdx.x == 0) *s_abort = !grid_sync_one(c, phase);
+    if (threadIdx.x == 0) *s_abort = !grid_sync_one(c, phase, rank, size);
     __syncthreads();
     return !*s_abort;
 }
@@ -169,6 +170,39 @@ __device__ __forceinline__ bool flag_wait(const Ctx& c, int ph, int b, unsigned 
         }
     }
     return ok;
+}
+
+// ---- checked builds (PIMC_CHECK): site-visit counters and index checks ----
+// A site visit of the even phase (kind 0), the odd phase (1) or a parameter
+// move's cache write (2) is counted per site; a test compares the counts with
+// the number of phases and moves (every site exactly once per phase).  An
+// index outside [0, M] sets kStatusBounds and the access is skipped.
+#ifdef PIMC_CHECK
+__device__ __forceinline__ bool chk_site(const Ctx& c, int kind, int64_t n)
+{
+    if (n < 0 || n > c.M) {
+        atomicOr(&c.st->status, kStatusBounds);
+        return false;
+    }
+    atomicAdd(c.chk + (int64_t)kind * c.ldx + n, 1u);
+    return true;
+}
+__device__ __forceinline__ void chk_move(const Ctx& c)
+{
+    atomicAdd((unsigned long long*)(c.chk + 3 * c.ldx), 1ull);
+}
+#else
+__device__ __forceinline__ constexpr bool chk_site(const Ctx&, int, int64_t) { return true; }
+__device__ __forceinline__ void chk_move(const Ctx&) {}
+#endif
+
+int checked_build()
+{
+#ifdef PIMC_CHECK
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 // Neighbourhood of site n loaded before its map is evaluated.
@@ -619,20 +653,25 @@ __device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
 }
 
 // Synchronisation policies of a chain's sweep.  GridSync: the chain is tiled
-// over all CTAs of a cooperative launch (grid barriers; each CTA adds its exact
-// partial into a slot of three integer accumulators before the barrier of a
-// parameter move and reads the total after it).  BlockSync: one CTA owns the
-// whole chain (CTA barriers, the CTA sum is the total).  Both give the same
-// bits for the same chain.  Slots rotate over three (a slot is cleared by CTA
-// 0 one move after its use, when every CTA has read it; the host clears all
-// before each launch).
+// over `size` CTAs -- all CTAs of a cooperative launch, or a group of a
+// batched launch -- the CTA of rank r owning tile r (barriers on the chain's
+// word; each CTA adds its exact partial into a slot of three integer
+// accumulators before the barrier of a parameter move and reads the total
+// after it).  BlockSync: one CTA owns the whole chain (CTA barriers, the CTA
+// sum is the total).  Both give the same bits for the same chain.  Slots
+// rotate over three (a slot is cleared by rank 0 one move after its use, when
+// every CTA has read it; all are cleared before each launch).
 struct GridSync {
+    int rank, size;
     static constexpr bool tiled = true;
     __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort, unsigned* phase) const
     {
-        return grid_barrier(c, s_abort, phase);
+        return grid_barrier(c, s_abort, phase, rank, size);
     }
-    __device__ __forceinline__ bool arrive_wait(const Ctx& c, unsigned* phase) const { return grid_sync_one(c, phase); }
+    __device__ __forceinline__ bool arrive_wait(const Ctx& c, unsigned* phase) const
+    {
+        return grid_sync_one(c, phase, rank, size);
+    }
     // thread 0, before the barrier
     __device__ __forceinline__ void publish(const Ctx& c, unsigned slot, const Fix3& f, Fix3*) const
     {
@@ -656,12 +695,12 @@ struct GridSync {
     // thread 0, after reading the total of `slot`: clear the previous slot
     __device__ __forceinline__ void recycle(const Ctx& c, unsigned slot) const
     {
-        if (blockIdx.x != 0) return;
+        if (rank != 0) return;
         unsigned long long* acc = (unsigned long long*)c.partials + 4 * ((slot + 2u) % 3u);
 #pragma unroll
         for (int j = 0; j < 4; ++j) __stcg(acc + j, 0ull);
     }
-    __device__ __forceinline__ bool lead() const { return blockIdx.x == 0; }
+    __device__ __forceinline__ bool lead() const { return rank == 0; }
 };
 
 struct BlockSync {
@@ -851,10 +890,12 @@ __device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<floa
             fc[a] = *(const float2*)(Fc + a * c.ldf + n);
         }
         hh_rk4_lanes<float2>(x, q2, *(const float2*)(I + n), dt2, hdt2, sdt2, fp);
+        if (chk_site(c, 2, n) && (!two || chk_site(c, 2, n + 1))) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            if (two) *(float2*)(Fn + a * c.ldf + n) = fp[a];
-            else Fn[a * c.ldf + n] = fp[a].x;
+            for (int a = 0; a < 4; ++a) {
+                if (two) *(float2*)(Fn + a * c.ldf + n) = fp[a];
+                else Fn[a * c.ldf + n] = fp[a].x;
+            }
         }
         const float2 t = rk4_term_lanes<float2, 4>(beta2, k.Rf, xn1, fp, fc);
         acc_add(acc, part, t.x);
@@ -894,6 +935,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             R* Fc = (R*)c.F[sh.fidx];
             const int64_t first = n0 + (((n0 & 1) != parity) ? 1 : 0);
             for (int64_t n = first + 2 * (int64_t)tid; n < n1; n += 2 * NT) {
+                if (!chk_site(c, parity, n)) continue;
                 my_acc[parity] += site_move<Model, R>(c, kc, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
                 my_prop[parity] += 1ull;
             }
@@ -905,6 +947,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
             if (!((sh.free_mask >> l) & 1u)) continue;
             if (tid == 0) sh.par_prop[l] += 1ull;
             if (!sh.inbox[l]) continue;  // out of the prior box: rejected without compute
+            if (tid == 0 && sync.lead()) chk_move(c);
             R pq[kMaxP];
 #pragma unroll
             for (int q = 0; q < kMaxP; ++q) pq[q] = pr[q];
@@ -919,12 +962,13 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
                     param_terms_paired<NT>(c, kc, n0, nend, pq, beta, Fc, Fn, part);
                 else
                     for (int64_t n = n0 + tid; n < nend; n += NT)
-                        fix_add(part, param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn));
+                        if (chk_site(c, 2, n)) fix_add(part, param_term<Model, R>(c, kc, n, pq, beta, Fc, Fn));
             } else {
                 // trapezoid: F(x_n, p') of the tile (and of the next tile's
                 // first site, recomputed here), then the residual changes
                 R g[D];
-                for (int64_t n = n0 + tid; n < n1; n += NT) trap_field<Model, R>(c, kc, n, pq, Fn, g);
+                for (int64_t n = n0 + tid; n < n1; n += NT)
+                    if (chk_site(c, 2, n)) trap_field<Model, R>(c, kc, n, pq, Fn, g);
                 if (n1 <= M && tid == NT - 1) {
                     trap_field<Model, R>(c, kc, n1, pq, nullptr, g);
 #pragma unroll
@@ -1090,7 +1134,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
         // ---- site phases: even sites, then odd sites (Sec. 4.1) ----
 #pragma unroll
         for (int parity = 0; parity < 2; ++parity) {
-            if (own && (int)(n & 1) == parity) {
+            if (own && (int)(n & 1) == parity && chk_site(c, parity, n)) {
                 // the proposal first: it needs no neighbour, so it overlaps the
                 // halo wait of the tile's boundary sites
                 R xp[D], gp[D], z[D], E;
@@ -1208,7 +1252,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                     apply_move<R, NT>(q, sh, l);
                     move_values<Model, R>(c, kc, trap, has_next, xr, xn, drive, drive1, q, f, fn);
                     if (has_next) fix_add(mine, move_term<R, D>(c, kc, trap, xr, xn, gr, gn, f, fn, beta));
-                    if (cached) {
+                    if (cached && chk_site(c, 2, n)) {
                         R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
                         for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
@@ -1248,6 +1292,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                             else {
                                 decide<R, NT>(sh, l, sync.total(c, slot, &sh.cta_fix));
                                 sync.recycle(c, slot);
+                                if (sync.lead()) chk_move(c);
                             }
                         }
                     } else if (l2 >= 0) {
@@ -1372,7 +1417,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
                             f[a] = acc ? fA[a] : fR[a];
                             fn[a] = acc ? fnA[a] : fnR[a];
                         }
-                        if (cached) {
+                        if (cached && chk_site(c, 2, n)) {
                             R* Fn = (R*)c.F[sh.fidx ^ 1u];
 #pragma unroll
                             for (int a = 0; a < D; ++a) Fn[a * c.ldf + n] = f[a];
@@ -1436,7 +1481,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_swe
     __shared__ SweepShared<R, kSweepBlock> sh;
     const int64_t n0 = (int64_t)blockIdx.x * c.tile;
     const int64_t n1 = min(n0 + c.tile, c.M + 1);
-    sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
+    sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // The parameter draws of the next n sweeps of a chain: out[2 (k NP + l)] = z,
@@ -1498,7 +1543,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) sweep_resident_kernel(Ctx c, i
     const int64_t n1 = min(n0 + c.tile, c.M + 1);
     if (threadIdx.x == 0) load_chain_state<Model, float, kSweepBlock>(c, sh);
     __syncthreads();
-    sweep_chain_resident<Model, float, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{});
+    sweep_chain_resident<Model, float, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{(int)blockIdx.x, (int)gridDim.x});
 }
 
 bool resident_fits(int prec, int64_t tile, int grid)
@@ -1506,26 +1551,50 @@ bool resident_fits(int prec, int64_t tile, int grid)
     return prec == 1 && tile <= kSweepBlock - 32 && (grid == 1 || (tile & 1) == 0);
 }
 
-// Many independent chains in one launch: CTA b runs, one after another, the
-// chains listed in order[first[b] .. first[b+1]) (whole chains, CTA-local
-// synchronisation, no inter-CTA waits).
+// Many chains in one launch: CTA b runs, one after another, the items
+// items[first[b] .. first[b+1]): a whole chain (CTA-local synchronisation), or
+// one tile of a long chain split over `size` CTAs, which then synchronise on
+// the chain's own barrier word and exact-sum slots (bounded waits).  Every
+// CTA's items follow one global order, so the CTAs of a split chain meet
+// without a cycle of waits; the launch is cooperative whenever a chain is
+// split.  Counters are keyed by the chain, never the CTA, so a chain's bits do
+// not depend on how it is tiled.
 // FP32: at least 512 / NT resident CTAs per SM (at most 128 registers a thread).
 template <class R, int NT> struct BatchBounds { static constexpr int min_blocks = 1; };
 template <int NT> struct BatchBounds<float, NT> { static constexpr int min_blocks = 512 / NT; };
 
 template <class Model, class R, int NT>
 __global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
-    batch_sweep_kernel(const Ctx* chains, const int* first, const int* order, int64_t n_sweeps, uint64_t seed)
+    batch_sweep_kernel(const Ctx* chains, const int* first, const BatchItem* items, int64_t n_sweeps, uint64_t seed)
 {
     __shared__ SweepShared<R, NT> sh;
     __shared__ Ctx cs;  // the current chain's context, read from shared memory
     for (int i = first[blockIdx.x]; i < first[blockIdx.x + 1]; ++i) {
+        const BatchItem it = items[i];
         if (threadIdx.x == 0) {
-            cs = chains[order[i]];
+            cs = chains[it.chain];
             cs.seed = seed;
         }
         __syncthreads();
-        sweep_chain<Model, R, NT>(cs, 0, cs.M + 1, n_sweeps, sh, BlockSync{});
+        if (it.size <= 1) {
+            sweep_chain<Model, R, NT>(cs, 0, cs.M + 1, n_sweeps, sh, BlockSync{});
+        } else {
+            // tile `rank` of `size` tiles of even length (as a chain's own launch tiles it)
+            int64_t tile = (cs.M + 1 + it.size - 1) / it.size;
+            tile += tile & 1;
+            const int64_t n0 = min((int64_t)it.rank * tile, cs.M + 1), n1 = min(n0 + tile, cs.M + 1);
+            const GridSync sync{it.rank, it.size};
+            if (threadIdx.x == 0) {
+                load_chain_state<Model, R, NT>(cs, sh);
+                // the exact-sum slots start at zero: rank 0 clears them before
+                // the group's first barrier
+                if (it.rank == 0)
+                    for (int j = 0; j < 12; ++j) __stcg((unsigned long long*)cs.partials + j, 0ull);
+            }
+            __syncthreads();
+            if (sync.barrier(cs, &sh.abort, &sh.bar_phase))
+                sweep_chain_general<Model, R, NT>(cs, n0, n1, n_sweeps, sh, sync);
+        }
         __syncthreads();
     }
 }
@@ -1589,11 +1658,18 @@ int sweep_max_grid(int model, int prec, int device, int resident)
 // ---- batched launch --------------------------------------------------------
 
 template <class Model, class R, int NT>
-static cudaError_t batch_t(const Ctx* chains, const int* first, const int* order, int n_ctas, int64_t n_sweeps,
-                           uint64_t seed, cudaStream_t s)
+static cudaError_t batch_t(const Ctx* chains, const int* first, const BatchItem* items, int n_ctas, int64_t n_sweeps,
+                           uint64_t seed, bool cooperative, cudaStream_t s)
 {
-    batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, 0, s>>>(chains, first, order, n_sweeps, seed);
-    return cudaGetLastError();
+    if (!cooperative) {
+        batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, 0, s>>>(chains, first, items, n_sweeps, seed);
+        return cudaGetLastError();
+    }
+    int64_t ns = n_sweeps;
+    uint64_t sd = seed;
+    void* args[] = {(void*)&chains, (void*)&first, (void*)&items, (void*)&ns, (void*)&sd};
+    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<Model, R, NT>, dim3(n_ctas), dim3(NT), args, 0,
+                                       s);
 }
 
 template <class Model, class R, int NT> static int batch_occ_t()
@@ -1630,10 +1706,11 @@ template <class Model, class R, int NT> static int batch_occ_t()
         return FN<Toy1D<float>, float, 256>(__VA_ARGS__);                                          \
     } while (0)
 
-cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first, const int* order,
-                               int n_ctas, int64_t n_sweeps, uint64_t seed, cudaStream_t s)
+cudaError_t launch_batch_sweep(int model, int prec, int nt, const Ctx* chains, const int* first,
+                               const BatchItem* items, int n_ctas, int64_t n_sweeps, uint64_t seed, bool cooperative,
+                               cudaStream_t s)
 {
-    PIMC_BATCH_DISPATCH(batch_t, chains, first, order, n_ctas, n_sweeps, seed, s);
+    PIMC_BATCH_DISPATCH(batch_t, chains, first, items, n_ctas, n_sweeps, seed, cooperative, s);
 }
 
 int batch_ctas_per_sm(int model, int prec, int nt) { PIMC_BATCH_DISPATCH(batch_occ_t); }

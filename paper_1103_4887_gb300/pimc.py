@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -35,7 +36,7 @@ EXPORTS = [
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
-    "pimc_debug_skip_arrive", "pimc_debug_fix_sum", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
+    "pimc_debug_skip_arrive", "pimc_debug_check_counts", "pimc_debug_fix_sum", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
     "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
 ]
@@ -117,6 +118,7 @@ def _declare(L):
         "pimc_set_wait_limit": [_vp, _i64],
         "pimc_debug_skip_arrive": [_vp, _int],
         "pimc_debug_fix_sum": [_vp, _i64, _int, _vp],
+        "pimc_debug_check_counts": [_vp, _vp, _vp, _vp, _vp, _vp, _int],
         "pimc_debug_lane_maps": [_vp, _vp, _vp, _d, _i64, _vp, _vp],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -124,9 +126,9 @@ def _declare(L):
         "pimc_batch_destroy": [_vp],
         "pimc_batch_sweep": [_vp, _i64, ctypes.c_uint64],
         "pimc_batch_sync": [_vp],
-        "pimc_batch_set_tuning": [_vp, _int, _int],
-        "pimc_batch_info": [_vp, _vp, _vp],
-        "pimc_batch_autotune": [_vp, _i64, ctypes.c_uint64, _vp, _vp],
+        "pimc_batch_set_tuning": [_vp, _int, _int, _int],
+        "pimc_batch_info": [_vp, _vp, _vp, _vp],
+        "pimc_batch_autotune": [_vp, _i64, ctypes.c_uint64, _vp, _vp, _vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -224,6 +226,10 @@ class Sampler:
             raise PimcError(r, self._L.pimc_last_error(self._h).decode())
 
     def close(self):
+        # a batch holding this handle goes first (its launches use the handle's
+        # stream and buffers)
+        for b in list(getattr(self, "_batches", ())):
+            b.close()
         if getattr(self, "_h", None):
             self._L.pimc_destroy(self._h)
             self._h = None
@@ -410,6 +416,17 @@ class Sampler:
         self._ck(self._L.pimc_launch_info(self._h, ctypes.byref(g), ctypes.byref(b)))
         return g.value, b.value
 
+    def check_counts(self, reset=True):
+        """Checked builds: per-site visit counts (even phase, odd phase,
+        parameter-move cache writes), the executed parameter moves and the
+        sticky status (test hook)."""
+        n1 = self.M + 1
+        ev, od, pa = (np.zeros(n1, dtype=np.uint32) for _ in range(3))
+        mv = np.zeros(1, dtype=np.uint64)
+        st = np.zeros(1, dtype=np.int32)
+        self._ck(self._L.pimc_debug_check_counts(self._h, _p(ev), _p(od), _p(pa), _p(mv), _p(st), 1 if reset else 0))
+        return ev, od, pa, int(mv[0]), int(st[0])
+
     def set_sweep_form(self, form):
         """'auto' (the resident form where it fits) or 'general'."""
         self._ck(self._L.pimc_set_sweep_form(self._h, {"auto": 0, "general": 1}.get(form, -1)))
@@ -439,6 +456,10 @@ class Batch:
         if r != OK:
             raise PimcError(r, self._L.pimc_batch_last_error(None).decode())
         self._b = b
+        for s in self.samplers:
+            if not hasattr(s, "_batches"):
+                s._batches = weakref.WeakSet()
+            s._batches.add(self)
 
     def _ck(self, r):
         if r != OK:
@@ -452,23 +473,28 @@ class Batch:
     def sync(self):
         self._ck(self._L.pimc_batch_sync(self._b))
 
-    def set_tuning(self, threads_per_cta, ctas_per_sm):
-        self._ck(self._L.pimc_batch_set_tuning(self._b, int(threads_per_cta), int(ctas_per_sm)))
+    def set_tuning(self, threads_per_cta, ctas_per_sm, ctas_per_chain=1):
+        self._ck(self._L.pimc_batch_set_tuning(self._b, int(threads_per_cta), int(ctas_per_sm), int(ctas_per_chain)))
 
     def info(self):
-        n, t = ctypes.c_int(), ctypes.c_int()
-        self._ck(self._L.pimc_batch_info(self._b, ctypes.byref(n), ctypes.byref(t)))
-        return n.value, t.value
+        """(CTAs of a launch, threads per CTA, chains split over several CTAs)."""
+        n, t, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.pimc_batch_info(self._b, ctypes.byref(n), ctypes.byref(t), ctypes.byref(sp)))
+        return n.value, t.value, sp.value
 
     def autotune(self, trial_sweeps, seed):
-        t, k = ctypes.c_int(), ctypes.c_int()
-        self._ck(self._L.pimc_batch_autotune(self._b, int(trial_sweeps), int(seed), ctypes.byref(t), ctypes.byref(k)))
-        return t.value, k.value
+        """Returns (threads per CTA, CTAs per SM, CTAs per long chain)."""
+        t, k, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._ck(self._L.pimc_batch_autotune(self._b, int(trial_sweeps), int(seed), ctypes.byref(t), ctypes.byref(k),
+                                             ctypes.byref(g)))
+        return t.value, k.value, g.value
 
     def close(self):
         if getattr(self, "_b", None):
             self._L.pimc_batch_destroy(self._b)
             self._b = None
+            for s in self.samplers:
+                getattr(s, "_batches", set()).discard(self)
 
     def __del__(self):
         try:

@@ -58,40 +58,53 @@ def test_batched_chains_equal_single_chain_runs_bitwise(prec, paper):
             assert np.array_equal(x, y)
 
 
-def test_tiling_does_not_change_a_chain():
-    """128- and 256-thread CTAs, few or many chains per CTA: the same chains,
-    bit for bit (the parameter-move sums are exact, so the order in which
-    threads add their terms does not matter)."""
-    ref = _make(pimc.FP64)
+@pytest.mark.parametrize("prec", [pimc.FP64, pimc.FP32_MIXED])
+def test_tiling_does_not_change_a_chain(prec):
+    """128- and 256-thread CTAs, few or many chains per CTA, long chains split
+    over up to 4 CTAs of the launch: the same chains, bit for bit (the
+    parameter-move sums are exact, so the order in which threads and CTAs add
+    their terms does not matter)."""
+    ref = _make(prec)
     b = pimc.Batch(ref)
     b.set_tuning(256, 1)
-    b.sweep(8, 5)
-    other = _make(pimc.FP64)
-    b2 = pimc.Batch(other)
-    b2.set_tuning(128, 0)
-    b2.sweep(8, 5)
-    for s1, s2 in zip(ref, other):
-        X1, p1 = s1.state()
-        X2, p2 = s2.state()
-        assert np.array_equal(X2, X1) and np.array_equal(p2, p1)
+    b.sweep(20, 5)
+    assert b.info()[2] == 0
+    for nt, k, g in ((128, 0, 1), (128, 0, 4), (256, 0, 2)):
+        other = _make(prec)
+        b2 = pimc.Batch(other)
+        b2.set_tuning(nt, k, g)
+        if g > 1:
+            assert b2.info()[2] >= 1  # the 2501-site chain (and at 128 threads the 1001-site one) is split
+        b2.sweep(7, 5)
+        b2.sweep(13, 5)  # a second launch continues the chains' barrier words and sums
+        for s1, s2 in zip(ref, other):
+            X1, p1 = s1.state()
+            X2, p2 = s2.state()
+            assert np.array_equal(X2, X1) and np.array_equal(p2, p1), (nt, k, g)
+            m1, v1, J1 = s1.moments()
+            m2, v2, J2 = s2.moments()
+            assert J1 == J2 == 3 and np.array_equal(m1, m2) and np.array_equal(v1, v2, equal_nan=True)
+            assert s1.sweep_counter() == s2.sweep_counter()
 
 
 def test_autotune_picks_a_valid_shape():
     chains = _make(pimc.FP32_MIXED)
     b = pimc.Batch(chains)
-    nt, k = b.autotune(3, 1)
-    assert nt in (128, 256) and k >= 1
-    n_ctas, t = b.info()
-    assert t == nt and 1 <= n_ctas <= len(chains)
+    nt, k, g = b.autotune(3, 1)
+    assert nt in (128, 256) and k >= 1 and g in (1, 2, 4)
+    n_ctas, t, n_split = b.info()
+    assert t == nt and 1 <= n_ctas and (n_split == 0) == (g == 1 or n_split == 0)
     b.sweep(5, 2)
     for s in chains:
         assert np.all(np.isfinite(s.state()[0]))
 
 
-def test_batched_chains_replay_against_oracle():
+@pytest.mark.parametrize("ctas_per_chain", [1, 4])
+def test_batched_chains_replay_against_oracle(ctas_per_chain):
     """The shortest and the longest chain of an FP64 batch (M = 37 and 5000,
     3 and 7 free parameters, chain ids 0 and 5) follow the oracle chain with
-    the same data, steps and chain id, one batched sweep at a time."""
+    the same data, steps and chain id, one batched sweep at a time; with
+    ctas_per_chain = 4 the long chains run as tiles over 2 to 4 CTAs."""
     Ms = [37, 800, 2500, 64, 1200, 5000]
     probs, samplers = [], []
     for k, M in enumerate(Ms):
@@ -101,7 +114,8 @@ def test_batched_chains_replay_against_oracle():
         probs.append(prob)
         samplers.append(s)
     b = pimc.Batch(samplers)
-    b.set_tuning(256, 0)
+    b.set_tuning(256, 0, ctas_per_chain)
+    assert (b.info()[2] > 0) == (ctas_per_chain > 1)
     watch = [0, 5]
     oracles = {}
     for k in watch:
