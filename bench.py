@@ -186,11 +186,18 @@ def cpu_baseline(prob, budget_s=12.0):
                       f"{el:.1f} s"}
 
 
+def workload_config(M):
+    """The workload a step runs, the same in both arms: HH with all 7
+    parameters free, N_skip sweeps a step, one statistics record a step."""
+    return {"workload": f"hh_M{M}_7free", "M": M, "n_free": 7, "sweeps_per_step": NSKIP, "n_skip": NSKIP}
+
+
 def run_reference(args):
-    """The serial FP64 oracle on one host core, same workload, metric and unit.
-    Each step is a bounded sample of the workload: one full sweep (a tenth of
-    the GPU arm's step); the timed steps stop after REF_BUDGET_S seconds so the
-    run ends within a few minutes whatever K is."""
+    """The serial FP64 oracle on one host core, same workload, step, metric and
+    unit: a step is N_skip full sweeps with one statistics record, after
+    W warm-up steps that adapt the steps (as the GPU arm's warm-up does); the
+    timed steps stop after REF_BUDGET_S seconds so the run ends within a few
+    minutes whatever K is."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -201,29 +208,29 @@ def run_reference(args):
     ch.set_data(prob.y, prob.I)
     ch.set_params(prob.p_init, prob.lo, prob.hi, prob.free)
     ch.set_steps(prob.sig_x, prob.sig_p)
-    ch.set_schedule(n_init=args.warmup, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
+    ch.set_schedule(n_init=args.warmup * NSKIP, n_skip=NSKIP, f_acc=0.4, alpha=0.5)
     for _ in range(args.warmup):
-        ch.sweep(1, SEED)
+        ch.sweep(NSKIP, SEED)
     times = []
     t_start = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        ch.sweep(1, SEED)
+        ch.sweep(NSKIP, SEED)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start > REF_BUDGET_S:
             break
     tot = sum(times)
     n = len(times)
-    value = (prob.M + 1) * n / tot
+    value = (prob.M + 1) * NSKIP * n / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * tot / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": 7,
-                                            "sweeps_per_step": 1, "l2": "host",
-                                            "steps_requested": args.steps},
+            "data": "synthetic", "config": workload_config(args.M),
+            "run": {"precision": "fp64", "where": "host, one core (serial oracle)", "steps_requested": args.steps},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} full sweeps of the M={args.M} workload (of {args.steps} requested, "
-                                       f"bounded at {REF_BUDGET_S:.0f} s), serial FP64 oracle"},
+                             "sample": f"{n} steps of {NSKIP} full sweeps of the M={args.M} workload (of "
+                                       f"{args.steps} requested, bounded at {REF_BUDGET_S:.0f} s), serial FP64 "
+                                       f"oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -890,10 +897,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == pimc.FP32_MIXED else "f64", "data": "synthetic",
-                "config": {"workload": f"hh_M{args.M}_7free", "M": args.M, "n_free": n_free,
-                           "precision": args.precision, "sweeps_per_step": NSKIP, "n_skip": NSKIP,
-                           "l2": "flushed (256 MiB write) before every timed step",
-                           "grid_block": grid_block, "form": form},
+                "config": workload_config(args.M),
+                "run": {"precision": args.precision, "l2": "flushed (256 MiB write) before every timed step",
+                        "grid_block": grid_block, "form": form},
                 # per step: the sweep kernel, and for the resident form the
                 # parameter-draws kernel before it
                 "gpu_launches": args.steps * (2 if form == "resident" else 1),

@@ -20,3 +20,16 @@ def test_reference_arm_json_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "hh_M200_7free"
+
+
+def test_both_arms_name_the_same_workload():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "3", "--M", "100"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    # the GPU arm's line uses workload_config(M) for its config as well
+    assert line["config"] == mod.workload_config(100)
+    assert line["config"]["sweeps_per_step"] == mod.NSKIP
