@@ -273,7 +273,27 @@ def _peak_fp32_tflops(n_sm, sm_mhz):
     return FLOP_PER_MAP / t_map / 1e12
 
 
-def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0):
+def map_ceiling():
+    """Maps per second of the FP32 HH map alone, iterated from registers by
+    every SM (pimc_debug_map_rate): one site a thread or two on the packed
+    f32x2 lanes, at 1 and 2 CTAs of 256 threads an SM -- the ceiling of a
+    sweep's map arithmetic on this device, beside the derived peak."""
+    import torch
+    from paper_1103_4887_gb300 import pimc
+    peaks, _ = load_peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_maps = n_sm * 128.0 * sm_mhz * 1e6 / FP32_OPS_PER_MAP  # derived peak in maps/s (FP32-bound)
+    out = {"derived_peak_maps_per_s": peak_maps}
+    for packed in (False, True):
+        for k in (1, 2):
+            r = pimc.debug_map_rate(packed, k, 4000)
+            out[f"{'packed' if packed else 'single'}_{k}cta_per_sm"] = {"maps_per_s": r, "frac_of_derived_peak":
+                                                                         r / peak_maps}
+    return out
+
+
+def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0, ceiling=None):
     """Observation-length sweep (HH, all 7 parameters free): per M, device time
     per sweep in one persistent launch (state L2-resident between sweeps, as in
     a sampling run), FP32-mixed and FP64, and the oracle timed on the host for a
@@ -312,6 +332,8 @@ def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0):
             if prec == pimc.FP32_MIXED:
                 tf = maps * FLOP_PER_MAP / (ms * 1e-3) / 1e12
                 entry.update({"achieved_tflops": tf, **roofline_fracs(maps, ms * 1e-3, n_sm, sm_mhz)})
+                if ceiling:
+                    entry["frac_of_map_ceiling"] = (maps / (ms * 1e-3)) / ceiling["packed_2cta_per_sm"]["maps_per_s"]
                 tr = traffic_of(form, M, 10)
                 if tr is not None:
                     entry["traffic_bytes_per_10_sweeps"] = tr
@@ -357,7 +379,9 @@ def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0):
 
 
 def run_sweep_M(args):
-    for row in sweep_M_rows(cpu_budget_s=30.0)["rows"]:
+    ceil = map_ceiling()
+    print(json.dumps({"map_ceiling": ceil}), flush=True)
+    for row in sweep_M_rows(cpu_budget_s=30.0, ceiling=ceil)["rows"]:
         print(json.dumps(row), flush=True)
 
 
@@ -702,6 +726,8 @@ def main():
                     help="no timing: 3 launches of one bench step per precision (a small case for ncu)")
     ap.add_argument("--profile-hmc", action="store_true",
                     help="no timing: 3 HMC trajectories per precision on the ESS workload (a small case for ncu)")
+    ap.add_argument("--map-ceiling", action="store_true",
+                    help="maps/s of the FP32 HH map alone from registers (single and packed lanes, 1 and 2 CTAs/SM)")
     ap.add_argument("--sweep-M", action="store_true",
                     help="observation-length sweep M = 2^10..2^20: site-updates/s and roofline per M, FP32-mixed "
                          "and FP64, with the serial oracle timed on the host for the same M")
@@ -724,6 +750,9 @@ def main():
         return
     if args.profile:
         run_profile_case(args)
+        return
+    if args.map_ceiling:
+        print(json.dumps(map_ceiling()), flush=True)
         return
     if args.profile_hmc:
         run_profile_hmc(args)
@@ -877,8 +906,12 @@ def main():
     if rank == 0 and world == 1 and not args.quick:
         samp.close()
         try:
-            extras["sweep_M"] = sweep_M_rows()
+            extras["map_ceiling"] = map_ceiling()
         except Exception as e:  # reported, not hidden
+            extras["map_ceiling"] = {"error": repr(e)}
+        try:
+            extras["sweep_M"] = sweep_M_rows(ceiling=extras["map_ceiling"])
+        except Exception as e:
             extras["sweep_M"] = {"error": repr(e)}
         try:
             extras["batch"] = run_batch(args)

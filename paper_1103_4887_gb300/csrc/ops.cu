@@ -298,4 +298,67 @@ cudaError_t launch_path_io(int prec, const Ctx& c, int D, double* dense, int to_
     return cudaGetLastError();
 }
 
+// Throughput probe of the FP32 HH map alone: every thread iterates x <- f(x)
+// `iters` times from registers (no memory traffic, no synchronisation), one
+// state (T = float) or two (T = float2, the packed lane form) a thread; the
+// sum of the final states goes to out[thread] so nothing is optimised away.
+// The rate it reaches is the ceiling of a sweep's map arithmetic.
+template <class T, int MINB>
+__global__ void __launch_bounds__(256, MINB) map_rate_kernel(int64_t iters, float* out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const float v0 = -65.0f + 0.001f * (float)(t & 1023), v1 = -60.0f + 0.001f * (float)(t & 511);
+    T x[4];
+    if constexpr (std::is_same<T, float2>::value) {
+        x[0] = make_float2(v0, v1);
+        x[1] = make_float2(0.05f, 0.06f);
+        x[2] = make_float2(0.6f, 0.58f);
+        x[3] = make_float2(0.32f, 0.33f);
+    } else {
+        x[0] = v0;
+        x[1] = 0.05f;
+        x[2] = 0.6f;
+        x[3] = 0.32f;
+    }
+    const float qs[kMaxP] = {120.f, 36.f, 0.3f, 50.f, -77.f, -54.4f, 1.f, 1.f};
+    T q[kMaxP];
+#pragma unroll
+    for (int j = 0; j < kMaxP; ++j) q[j] = splat<T>(qs[j]);
+    const float dt = 0.02f;
+    const T I = splat<T>(10.0f), dtv = splat<T>(dt), hdt = splat<T>(__fmul_rn(0.5f, dt)),
+            sdt = splat<T>(__fdiv_rn(dt, 6.0f));
+    for (int64_t it = 0; it < iters; ++it) {
+        T f[4];
+        hh_rk4_lanes<T>(x, q, I, dtv, hdt, sdt, f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a] = f[a];
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if constexpr (std::is_same<T, float2>::value) acc += x[a].x + x[a].y;
+        else acc += x[a];
+    }
+    out[t] = acc;
+}
+
+template <class T, int MINB>
+static cudaError_t map_rate_t(int n_sm, int64_t iters, float* out, cudaStream_t s)
+{
+    map_rate_kernel<T, MINB><<<n_sm * MINB, 256, 0, s>>>(iters, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_rate(int packed, int ctas_per_sm, int n_sm, int64_t iters, float* out, cudaStream_t s)
+{
+    if (packed) {
+        if (ctas_per_sm == 1) return map_rate_t<float2, 1>(n_sm, iters, out, s);
+        if (ctas_per_sm == 2) return map_rate_t<float2, 2>(n_sm, iters, out, s);
+        return map_rate_t<float2, 4>(n_sm, iters, out, s);
+    }
+    if (ctas_per_sm == 1) return map_rate_t<float, 1>(n_sm, iters, out, s);
+    if (ctas_per_sm == 2) return map_rate_t<float, 2>(n_sm, iters, out, s);
+    return map_rate_t<float, 4>(n_sm, iters, out, s);
+}
+
 }  // namespace pimc

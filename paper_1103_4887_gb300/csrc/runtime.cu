@@ -17,6 +17,13 @@
 
 using namespace pimc;
 
+namespace pimc {
+// Map-throughput probe (ops.cu): ctas_per_sm (1, 2 or 4) CTAs of 256 threads
+// per SM, each thread iterating the FP32 HH map `iters` times (two lanes when
+// packed); out: n_sm * ctas_per_sm * 256 floats.
+cudaError_t launch_map_rate(int packed, int ctas_per_sm, int n_sm, int64_t iters, float* out, cudaStream_t s);
+}  // namespace pimc
+
 struct pimc_handle_s {
     int model = 0, D = 0, NP = 0, prec = 0;
     int scheme = 0, proposal = 0;
@@ -970,6 +977,40 @@ int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out
         set_thread_error(cudaGetErrorString(e));
         return PIMC_ERR_CUDA;
     }
+    return PIMC_OK;
+}
+
+int pimc_debug_map_rate(int packed, int ctas_per_sm, int64_t iters, double* maps_per_s)
+{
+    if ((ctas_per_sm != 1 && ctas_per_sm != 2 && ctas_per_sm != 4) || iters < 1 || iters > ((int64_t)1 << 24) ||
+        !maps_per_s) {
+        set_thread_error("pimc_debug_map_rate: ctas_per_sm in {1, 2, 4}, 1 <= iters <= 2^24 and an output required");
+        return PIMC_ERR_ARG;
+    }
+    int dev = 0, n_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    float* out = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float) * (size_t)n_sm * ctas_per_sm * 256);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch_map_rate(packed, ctas_per_sm, n_sm, 16, out, 0);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = launch_map_rate(packed, ctas_per_sm, n_sm, iters, out, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) {
+        set_thread_error(cudaGetErrorString(e));
+        return PIMC_ERR_CUDA;
+    }
+    const double maps = (double)n_sm * ctas_per_sm * 256 * (double)iters * (packed ? 2.0 : 1.0);
+    *maps_per_s = maps / (ms * 1e-3);
     return PIMC_OK;
 }
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
     "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
-    "pimc_debug_skip_arrive", "pimc_debug_check_counts", "pimc_debug_fix_sum", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
+    "pimc_debug_skip_arrive", "pimc_debug_check_counts", "pimc_debug_fix_sum", "pimc_debug_map_rate", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
     "pimc_batch_set_tuning", "pimc_batch_info", "pimc_batch_autotune",
 ]
@@ -120,6 +120,7 @@ def _declare(L):
         "pimc_debug_fix_sum": [_vp, _i64, _int, _vp],
         "pimc_debug_check_counts": [_vp, _vp, _vp, _vp, _vp, _vp, _int],
         "pimc_debug_lane_maps": [_vp, _vp, _vp, _d, _i64, _vp, _vp],
+        "pimc_debug_map_rate": [_int, _int, _i64, _vp],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
         "pimc_batch_create": [_vp, _vp, _int],
@@ -170,6 +171,16 @@ def debug_fix_sum(terms, as_float=False, acc128=False):
     out = np.zeros(1)
     mode = 2 if acc128 else (1 if as_float else 0)
     r = L.pimc_debug_fix_sum(_p(t), int(t.size), mode, _p(out))
+    if r != OK:
+        raise PimcError(r, L.pimc_last_error(None).decode())
+    return float(out[0])
+
+
+def debug_map_rate(packed, ctas_per_sm, iters=2000):
+    """FP32 HH maps per second of the map alone, iterated from registers (test hook)."""
+    L = load()
+    out = np.zeros(1)
+    r = L.pimc_debug_map_rate(1 if packed else 0, int(ctas_per_sm), int(iters), _p(out))
     if r != OK:
         raise PimcError(r, L.pimc_last_error(None).decode())
     return float(out[0])

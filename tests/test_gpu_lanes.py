@@ -61,3 +61,11 @@ def test_rejects_bad_arguments():
     with pytest.raises(pimc.PimcError) as e:
         pimc.debug_lane_maps(X, I, synth.HH_TRUTH, 0.0)
     assert e.value.code == pimc.ERR_ARG
+
+
+def test_map_rate_probe_is_positive_and_packed_not_slower():
+    single = pimc.debug_map_rate(False, 2, 500)
+    packed = pimc.debug_map_rate(True, 2, 500)
+    assert single > 0 and packed > 0.9 * single
+    with pytest.raises(pimc.PimcError):
+        pimc.debug_map_rate(True, 3, 500)
