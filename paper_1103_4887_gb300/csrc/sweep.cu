@@ -861,35 +861,102 @@ __device__ __forceinline__ void store_chain_state(const Ctx& c, SweepShared<R, N
     __syncthreads();
 }
 
+// Shared-memory staging of the paired parameter-move loop: per thread and
+// buffer, the operands of one pair (n, n + 1) -- x_n, x_{n+1} (4 float2),
+// x_{n+2} (4 floats), the cached f_n, f_{n+1} (4 float2) and the drive
+// (float2) -- copied from global memory with cp.async while the thread
+// evaluates the pair before, two buffers in turn.  Each thread reads only its
+// own slots, so no CTA barrier is needed; the layout is [buffer][field][thread]
+// (consecutive threads, consecutive words: no bank conflicts).  It lives in
+// the kernel's dynamic shared memory.
+template <int NT> struct PairStage {
+    float2 x[2][4][NT];
+    float2 fc[2][4][NT];
+    float2 I[2][NT];
+    float xn2[2][4][NT];
+};
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// Dynamic shared memory a sweep kernel of this model and arithmetic type is
+// launched with (the paired loop's staging; none for the other forms).
+template <class Model, class R, int NT> struct StageBytes { static constexpr int value = 0; };
+template <int NT> struct StageBytes<HH<float>, float, NT> { static constexpr int value = (int)sizeof(PairStage<NT>); };
+
 // RK4 scheme, FP32 HH: the sites [n0, nend) of a parameter move two at a time,
 // (n, n + 1) with n - n0 even, on the packed f32x2 lane form -- per site the
 // same bits as param_term.  n0 is even (tiles have even length), so the pair
-// loads and stores are 8-byte aligned; an unpaired last site is lane x alone
-// (lane y then reads x_{n+1}, f_{n+1}, I_{n+1}, inside the rows, and is
-// dropped).
+// copies are 8-byte aligned; an unpaired last site is lane x alone (lane y
+// then reads x_{n+1}, f_{n+1}, I_{n+1}, inside the rows, and is dropped).  The
+// operands come through the shared-memory staging, the next pair's copies in
+// flight while this pair is evaluated; every launch of a kernel that runs this
+// loop passes the staging's size (a kernel without it sets kStatusBounds and
+// skips the move's terms rather than touch memory it does not have).
 template <int NT>
 __device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<float>& k, int64_t n0, int64_t nend,
                                                    const float* pq, float beta, const float* Fc, float* Fn,
                                                    Fix3& part)
 {
+    extern __shared__ __align__(16) unsigned char pimc_dyn_smem[];
+    if (dynamic_smem_bytes() < sizeof(PairStage<NT>)) {
+        if (threadIdx.x == 0) atomicOr(&c.st->status, kStatusBounds);
+        return;
+    }
     const float* X = (const float*)c.X;
     const float* I = (const float*)c.I;
+    const int tid = threadIdx.x;
     float2 q2[kMaxP];
 #pragma unroll
     for (int j = 0; j < kMaxP; ++j) q2[j] = splat<float2>(pq[j]);
     const float2 dt2 = splat<float2>(k.dt), beta2 = splat<float2>(beta);
     const float2 hdt2 = splat<float2>(__fmul_rn(0.5f, k.dt)), sdt2 = splat<float2>(__fdiv_rn(k.dt, 6.0f));
     Acc128 acc{0ull, 0ull};
-    for (int64_t n = n0 + 2 * (int64_t)threadIdx.x; n < nend; n += 2 * NT) {
+    PairStage<NT>* st = (PairStage<NT>*)pimc_dyn_smem;
+    int64_t n = n0 + 2 * (int64_t)tid;
+    // the copies of pair (m, m + 1) into buffer b (m < nend)
+    auto issue = [&](int b, int64_t m) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            cp_async8(&st->x[b][a][tid], X + a * c.ldx + m);
+            cp_async8(&st->fc[b][a][tid], Fc + a * c.ldf + m);
+            if (m + 1 < nend) cp_async4(&st->xn2[b][a][tid], X + a * c.ldx + m + 2);
+            else st->xn2[b][a][tid] = 0.0f;
+        }
+        cp_async8(&st->I[b][tid], I + m);
+    };
+    if (n < nend) issue(0, n);
+    cp_async_commit();
+    for (int buf = 0; n < nend; n += 2 * NT, buf ^= 1) {
         const bool two = n + 1 < nend;
+        if (n + 2 * NT < nend) issue(buf ^ 1, n + 2 * NT);
+        cp_async_commit();
+        cp_async_wait<1>();  // this pair's group has landed
         float2 x[4], xn1[4], fc[4], fp[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            x[a] = *(const float2*)(X + a * c.ldx + n);
-            xn1[a] = make_float2(x[a].y, two ? X[a * c.ldx + n + 2] : 0.0f);
-            fc[a] = *(const float2*)(Fc + a * c.ldf + n);
+            x[a] = st->x[buf][a][tid];
+            xn1[a] = make_float2(x[a].y, st->xn2[buf][a][tid]);
+            fc[a] = st->fc[buf][a][tid];
         }
-        hh_rk4_lanes<float2>(x, q2, *(const float2*)(I + n), dt2, hdt2, sdt2, fp);
+        hh_rk4_lanes<float2>(x, q2, st->I[buf][tid], dt2, hdt2, sdt2, fp);
         if (chk_site(c, 2, n) && (!two || chk_site(c, 2, n + 1))) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
@@ -901,6 +968,7 @@ __device__ __forceinline__ void param_terms_paired(const Ctx& c, const Coef<floa
         acc_add(acc, part, t.x);
         if (two) acc_add(acc, part, t.y);
     }
+    cp_async_wait<0>();
     acc_fold(acc, part);
 }
 
@@ -1475,8 +1543,12 @@ __device__ void sweep_chain(const Ctx& c, int64_t n0, int64_t n1, int64_t n_swee
     sweep_chain_general<Model, R, NT>(c, n0, n1, n_sweeps, sh, sync);
 }
 
+// FP32: two resident CTAs an SM (at most 128 registers a thread).
+template <class R> struct SweepBounds { static constexpr int min_blocks = 1; };
+template <> struct SweepBounds<float> { static constexpr int min_blocks = 2; };
+
 template <class Model, class R>
-__global__ void __launch_bounds__(kSweepBlock) sweep_kernel(Ctx c, int64_t n_sweeps)
+__global__ void __launch_bounds__(kSweepBlock, SweepBounds<R>::min_blocks) sweep_kernel(Ctx c, int64_t n_sweeps)
 {
     __shared__ SweepShared<R, kSweepBlock> sh;
     const int64_t n0 = (int64_t)blockIdx.x * c.tile;
@@ -1608,6 +1680,18 @@ template <class Model> struct SweepKernels<Model, float> {
     static const void* resident() { return (const void*)sweep_resident_kernel<Model>; }
 };
 
+// Opt a kernel in to `bytes` of dynamic shared memory (above the default
+// limit once the static part is added); once per kernel.
+template <class K>
+static cudaError_t allow_dynamic_smem(K* kernel, int bytes)
+{
+    static bool done = false;
+    if (bytes == 0 || done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <class Model, class R>
 static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s)
 {
@@ -1627,13 +1711,16 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
         if (e != cudaSuccess) return e;
     }
     const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, 0, s);
+    const int smem = res ? 0 : StageBytes<Model, R, kSweepBlock>::value;
+    const cudaError_t e = allow_dynamic_smem(sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, (size_t)smem, s);
 }
 
-static int max_grid_of(const void* k, int device)
+static int max_grid_of(const void* k, int device, int smem)
 {
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSweepBlock, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSweepBlock, (size_t)smem) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     return per_sm * sms;
 }
@@ -1641,8 +1728,9 @@ static int max_grid_of(const void* k, int device)
 template <class Model, class R>
 static int max_grid_t(int device, int resident)
 {
+    if (allow_dynamic_smem(sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value) != cudaSuccess) return 0;
     const void* k = resident ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
-    return k ? max_grid_of(k, device) : 0;
+    return k ? max_grid_of(k, device, resident ? 0 : StageBytes<Model, R, kSweepBlock>::value) : 0;
 }
 
 cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s)
@@ -1661,21 +1749,27 @@ template <class Model, class R, int NT>
 static cudaError_t batch_t(const Ctx* chains, const int* first, const BatchItem* items, int n_ctas, int64_t n_sweeps,
                            uint64_t seed, bool cooperative, cudaStream_t s)
 {
+    constexpr int smem = StageBytes<Model, R, NT>::value;
+    const cudaError_t e = allow_dynamic_smem(batch_sweep_kernel<Model, R, NT>, smem);
+    if (e != cudaSuccess) return e;
     if (!cooperative) {
-        batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, 0, s>>>(chains, first, items, n_sweeps, seed);
+        batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, smem, s>>>(chains, first, items, n_sweeps, seed);
         return cudaGetLastError();
     }
     int64_t ns = n_sweeps;
     uint64_t sd = seed;
     void* args[] = {(void*)&chains, (void*)&first, (void*)&items, (void*)&ns, (void*)&sd};
-    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<Model, R, NT>, dim3(n_ctas), dim3(NT), args, 0,
-                                       s);
+    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<Model, R, NT>, dim3(n_ctas), dim3(NT), args,
+                                       (size_t)smem, s);
 }
 
 template <class Model, class R, int NT> static int batch_occ_t()
 {
+    constexpr int smem = StageBytes<Model, R, NT>::value;
+    if (allow_dynamic_smem(batch_sweep_kernel<Model, R, NT>, smem) != cudaSuccess) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<Model, R, NT>, NT, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<Model, R, NT>, NT, (size_t)smem) !=
+        cudaSuccess)
         return 0;
     return per_sm;
 }
