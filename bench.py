@@ -290,6 +290,8 @@ def map_ceiling():
             r = pimc.debug_map_rate(packed, k, 4000)
             out[f"{'packed' if packed else 'single'}_{k}cta_per_sm"] = {"maps_per_s": r, "frac_of_derived_peak":
                                                                          r / peak_maps}
+    # the FP64 map (software exponentials on the FP64 pipe), the plain sweep's ceiling
+    out["fp64_1cta_per_sm"] = {"maps_per_s": pimc.debug_map_rate(False, 1, 200, fp64=True)}
     return out
 
 
@@ -340,9 +342,11 @@ def sweep_M_rows(exps=range(10, 21, 2), cpu_budget_s=4.0, ceiling=None):
                     entry["dram_gbs"] = tr / (10 * ms * 1e-3) / 1e9
             else:
                 # FP64 transcendental functions are software sequences on the FP64
-                # pipe: the achieved rate is stated as maps/s; the FP32 count does
-                # not apply
+                # pipe: the achieved rate is stated as maps/s against the FP64 map's
+                # own measured ceiling; the FP32 count does not apply
                 entry["note"] = "FP64 pipe-bound (software exp); compare maps/s"
+                if ceiling and "fp64_1cta_per_sm" in ceiling:
+                    entry["frac_of_fp64_map_ceiling"] = (maps / (ms * 1e-3)) / ceiling["fp64_1cta_per_sm"]["maps_per_s"]
             row[name] = entry
             s.close()
         n_cpu = 100 if M <= 1 << 12 else (10 if M <= 1 << 16 else 2)

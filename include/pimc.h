@@ -362,14 +362,15 @@ int pimc_debug_skip_arrive(pimc_t h, int cta);
  * general sweep form use (same result).  No handle; synchronous.
  * PIMC_ERR_ARG for n < 0 or n > 2^20, PIMC_ERR_CUDA on a device error. */
 int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out);
-/* Throughput probe of the FP32 form of the model map f (the RK4 map of Eq.
- * (action)'s model-error term): ctas_per_sm (1, 2 or 4) CTAs of 256 threads
- * on every SM, each thread iterating f from registers `iters` times (1 <=
- * iters <= 2^24), one state a thread, or two as the lanes of the packed
- * f32x2 form when packed != 0; *maps_per_s (host) receives the rate.  No
- * memory traffic and no synchronisation: the ceiling a sweep's map
- * arithmetic can reach on this device.  Synchronous, on the current device;
- * PIMC_ERR_ARG for arguments out of range, PIMC_ERR_CUDA on a device error. */
+/* Throughput probe of the model map f (the RK4 map of Eq. (action)'s
+ * model-error term): ctas_per_sm (1, 2 or 4) CTAs of 256 threads on every SM,
+ * each thread iterating f from registers `iters` times (1 <= iters <= 2^24):
+ * packed = 0, the FP32 form, one state a thread; 1, two states as the lanes
+ * of the packed f32x2 form; 2, the FP64 form, one state a thread.
+ * *maps_per_s (host) receives the rate.  No memory traffic and no
+ * synchronisation: the ceiling a sweep's map arithmetic can reach on this
+ * device.  Synchronous, on the current device; PIMC_ERR_ARG for arguments out
+ * of range, PIMC_ERR_CUDA on a device error. */
 int pimc_debug_map_rate(int packed, int ctas_per_sm, int64_t iters, double* maps_per_s);
 /* The FP32 form of the model map f (one classical RK4 step of the HH field of
  * Sec. 5.1 with the textbook rates, drive held over the step; the map of the

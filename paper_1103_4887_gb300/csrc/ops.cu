@@ -349,8 +349,33 @@ static cudaError_t map_rate_t(int n_sm, int64_t iters, float* out, cudaStream_t 
     return cudaGetLastError();
 }
 
+// The FP64 form of the same probe: the FP64 HH map (rk4_map<HH<double>>, the
+// map of the plain FP64 sweep) iterated from registers, one state a thread.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) map_rate_fp64_kernel(int64_t iters, float* out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double x[4] = {-65.0 + 0.001 * (double)(t & 1023), 0.05, 0.6, 0.32};
+    const double ps[kMaxP] = {120.0, 36.0, 0.3, 50.0, -77.0, -54.4, 1.0, 0.0};
+    double q[kMaxP];
+    HH<double>::prep(ps, q);
+    for (int64_t it = 0; it < iters; ++it) {
+        double f[4];
+        rk4_map<HH<double>, double>(x, q, 10.0, 0.02, f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a] = f[a];
+    }
+    out[t] = (float)(x[0] + x[1] + x[2] + x[3]);
+}
+
 cudaError_t launch_map_rate(int packed, int ctas_per_sm, int n_sm, int64_t iters, float* out, cudaStream_t s)
 {
+    if (packed == 2) {  // FP64
+        if (ctas_per_sm == 1) map_rate_fp64_kernel<1><<<n_sm, 256, 0, s>>>(iters, out);
+        else if (ctas_per_sm == 2) map_rate_fp64_kernel<2><<<n_sm * 2, 256, 0, s>>>(iters, out);
+        else map_rate_fp64_kernel<4><<<n_sm * 4, 256, 0, s>>>(iters, out);
+        return cudaGetLastError();
+    }
     if (packed) {
         if (ctas_per_sm == 1) return map_rate_t<float2, 1>(n_sm, iters, out, s);
         if (ctas_per_sm == 2) return map_rate_t<float2, 2>(n_sm, iters, out, s);

@@ -19,8 +19,9 @@ using namespace pimc;
 
 namespace pimc {
 // Map-throughput probe (ops.cu): ctas_per_sm (1, 2 or 4) CTAs of 256 threads
-// per SM, each thread iterating the FP32 HH map `iters` times (two lanes when
-// packed); out: n_sm * ctas_per_sm * 256 floats.
+// per SM, each thread iterating the HH map `iters` times: FP32 (packed 0),
+// FP32 on two packed lanes (1) or FP64 (2); out: n_sm * ctas_per_sm * 256
+// floats.
 cudaError_t launch_map_rate(int packed, int ctas_per_sm, int n_sm, int64_t iters, float* out, cudaStream_t s);
 }  // namespace pimc
 
@@ -983,8 +984,9 @@ int pimc_debug_fix_sum(const double* terms, int64_t n, int as_float, double* out
 int pimc_debug_map_rate(int packed, int ctas_per_sm, int64_t iters, double* maps_per_s)
 {
     if ((ctas_per_sm != 1 && ctas_per_sm != 2 && ctas_per_sm != 4) || iters < 1 || iters > ((int64_t)1 << 24) ||
-        !maps_per_s) {
-        set_thread_error("pimc_debug_map_rate: ctas_per_sm in {1, 2, 4}, 1 <= iters <= 2^24 and an output required");
+        !maps_per_s || packed < 0 || packed > 2) {
+        set_thread_error("pimc_debug_map_rate: form in {0, 1, 2}, ctas_per_sm in {1, 2, 4}, 1 <= iters <= 2^24 "
+                         "and an output required");
         return PIMC_ERR_ARG;
     }
     int dev = 0, n_sm = 0;
@@ -1009,7 +1011,7 @@ int pimc_debug_map_rate(int packed, int ctas_per_sm, int64_t iters, double* maps
         set_thread_error(cudaGetErrorString(e));
         return PIMC_ERR_CUDA;
     }
-    const double maps = (double)n_sm * ctas_per_sm * 256 * (double)iters * (packed ? 2.0 : 1.0);
+    const double maps = (double)n_sm * ctas_per_sm * 256 * (double)iters * (packed == 1 ? 2.0 : 1.0);
     *maps_per_s = maps / (ms * 1e-3);
     return PIMC_OK;
 }

@@ -176,11 +176,13 @@ def debug_fix_sum(terms, as_float=False, acc128=False):
     return float(out[0])
 
 
-def debug_map_rate(packed, ctas_per_sm, iters=2000):
-    """FP32 HH maps per second of the map alone, iterated from registers (test hook)."""
+def debug_map_rate(packed, ctas_per_sm, iters=2000, fp64=False):
+    """HH maps per second of the map alone, iterated from registers (test
+    hook): FP32 single or packed lanes, or the FP64 map."""
     L = load()
     out = np.zeros(1)
-    r = L.pimc_debug_map_rate(1 if packed else 0, int(ctas_per_sm), int(iters), _p(out))
+    form = 2 if fp64 else (1 if packed else 0)
+    r = L.pimc_debug_map_rate(form, int(ctas_per_sm), int(iters), _p(out))
     if r != OK:
         raise PimcError(r, L.pimc_last_error(None).decode())
     return float(out[0])

@@ -67,5 +67,7 @@ def test_map_rate_probe_is_positive_and_packed_not_slower():
     single = pimc.debug_map_rate(False, 2, 500)
     packed = pimc.debug_map_rate(True, 2, 500)
     assert single > 0 and packed > 0.9 * single
+    fp64 = pimc.debug_map_rate(False, 1, 50, fp64=True)
+    assert 0 < fp64 < single
     with pytest.raises(pimc.PimcError):
         pimc.debug_map_rate(True, 3, 500)
