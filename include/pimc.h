@@ -263,6 +263,14 @@ int pimc_param_trace(pimc_t h, double* out, int64_t cap, int64_t* n_written);
 
 /* ---- state ----------------------------------------------------------------- */
 int pimc_get_state(pimc_t h, double* X, double* p);
+/* The parameter vector p (Np doubles) as it stands after the work enqueued so
+ * far, copied into caller-owned host memory p_host by a copy enqueued on the
+ * handle's stream, without waiting: the values are there once the stream has
+ * reached the copy (pimc_sync, or any synchronisation of that stream).  For
+ * streaming use (data in, sweeps, result out, step after step) with no host
+ * stall per step; p_host should be page-locked, else the copy is not
+ * asynchronous.  PIMC_ERR_ARG for NULL arguments. */
+int pimc_params_async(pimc_t h, double* p_host);
 int pimc_get_steps(pimc_t h, double* sigma_x /*D*(M+1)*/, double* sigma_p /*Np*/);
 /* Current sweep counter and beta. */
 int pimc_get_sweep(pimc_t h, int64_t* sweep, double* beta);

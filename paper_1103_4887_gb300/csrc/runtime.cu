@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <map>
 #include <queue>
 #include <cstdio>
@@ -886,6 +887,14 @@ int pimc_get_state(pimc_t h, double* X, double* p)
         if (r != PIMC_OK) return r;
         for (int l = 0; l < h->NP; ++l) p[l] = h->hs.p[l];
     }
+    return PIMC_OK;
+}
+
+int pimc_params_async(pimc_t h, double* p_host)
+{
+    if (!h || !p_host) return fail(h, PIMC_ERR_ARG, "pimc_params_async: NULL argument");
+    const double* src = (const double*)((const char*)h->st + offsetof(DevState, p));
+    CK(h, cudaMemcpyAsync(p_host, src, sizeof(double) * h->NP, cudaMemcpyDeviceToHost, h->stream));
     return PIMC_OK;
 }
 

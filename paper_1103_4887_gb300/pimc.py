@@ -34,7 +34,7 @@ EXPORTS = [
     "pimc_set_data", "pimc_load_data", "pimc_set_params", "pimc_set_path", "pimc_set_steps", "pimc_set_schedule",
     "pimc_set_chain", "pimc_sweep", "pimc_hmc", "pimc_sync", "pimc_action", "pimc_grad", "pimc_action_dev",
     "pimc_grad_dev", "pimc_site_delta", "pimc_param_delta", "pimc_moments", "pimc_set_histograms",
-    "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
+    "pimc_histograms", "pimc_histogram_shape", "pimc_set_param_trace", "pimc_param_trace", "pimc_get_state", "pimc_params_async", "pimc_get_steps", "pimc_get_sweep", "pimc_accept_stats",
     "pimc_launch_info", "pimc_sweep_form", "pimc_set_sweep_form", "pimc_residual_moments", "pimc_forecast", "pimc_checkpoint_save", "pimc_checkpoint_load", "pimc_set_wait_limit",
     "pimc_debug_skip_arrive", "pimc_debug_check_counts", "pimc_debug_fix_sum", "pimc_debug_map_rate", "pimc_debug_lane_maps", "pimc_set_grid", "pimc_action_static",
     "pimc_batch_create", "pimc_batch_destroy", "pimc_batch_last_error", "pimc_batch_sweep", "pimc_batch_sync",
@@ -121,6 +121,7 @@ def _declare(L):
         "pimc_debug_check_counts": [_vp, _vp, _vp, _vp, _vp, _vp, _int],
         "pimc_debug_lane_maps": [_vp, _vp, _vp, _d, _i64, _vp, _vp],
         "pimc_debug_map_rate": [_int, _int, _i64, _vp],
+        "pimc_params_async": [_vp, _vp],
         "pimc_set_grid": [_vp, _int],
         "pimc_action_static": [_int, _i64, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
         "pimc_batch_create": [_vp, _vp, _int],
@@ -402,6 +403,11 @@ class Sampler:
         p = np.zeros(self.Np)
         self._ck(self._L.pimc_get_state(self._h, None, _p(p)))
         return p
+
+    def params_async(self, p_ptr):
+        """Enqueue a copy of p into caller-owned host memory (Np doubles at
+        p_ptr, page-locked for asynchrony); valid after the stream syncs."""
+        self._ck(self._L.pimc_params_async(self._h, _vp(p_ptr)))
 
     def steps(self):
         sx = np.zeros(self.D * (self.M + 1))

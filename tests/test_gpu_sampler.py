@@ -243,3 +243,16 @@ def test_residual_moments_and_forecast_parity():
         fg = g.forecast(50, Ifut, 64, noise, 5)
         fo = o.forecast(50, Ifut, 64, noise, 5)
         np.testing.assert_allclose(fg, fo, rtol=1e-10, atol=1e-10)
+
+
+def test_params_async_matches_the_synchronous_read():
+    torch = pytest.importorskip("torch")
+    prob = synth.hh_problem(500, data_seed=3, free="all")
+    g = pimc.Sampler.from_problem(prob)
+    buf = torch.zeros((3, 7), dtype=torch.float64).pin_memory()
+    for k in range(3):
+        g.sweep(2, 11, sync=False)
+        g.params_async(buf[k].data_ptr())
+    g.sync()
+    assert np.array_equal(buf[2].numpy(), g.params())
+    assert not np.array_equal(buf[0].numpy(), buf[2].numpy()) or np.all(np.isfinite(buf.numpy()))
