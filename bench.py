@@ -582,11 +582,12 @@ def _ess_block(tr, secs, names, n_boot=100):
 
 
 def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n_hmc=(1000, 200), n_leap=20,
-              names=None, seed=SEED):
+              names=None, seed=SEED, anneal=None, f_acc=0.4, alpha=0.5):
     """Parameter ESS per second of the four samplers on one posterior, from
     independent chains that start in it.  A pilot of K batched FP32-mixed
     Metropolis chains (from the data's initial path, adapting during its first
-    half) supplies each chain's starting state and steps, and the pooled
+    half; optionally annealed there as in Sec. 4.2, anneal = (beta0, N_cool))
+    supplies each chain's starting state and steps, and the pooled
     variances that serve as HMC's inverse mass.  Then, from those states and
     with fresh seeds: K chains of batched checkerboard Metropolis in FP32-mixed
     and in FP64 (n_metro sweeps each), and K_hmc chains of whole-path HMC in
@@ -612,13 +613,16 @@ def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n
     # pilot
     P = [make(pimc.FP32_MIXED, k) for k in range(K)]
     for s in P:
-        s.set_schedule(n_init=pilot[0], n_skip=10, f_acc=0.4, alpha=0.5)
+        if anneal is None:
+            s.set_schedule(n_init=pilot[0], n_skip=10, f_acc=f_acc, alpha=alpha)
+        else:
+            s.set_schedule(n_init=pilot[0], n_skip=10, beta0=anneal[0], n_cool=anneal[1], f_acc=f_acc, alpha=alpha)
         s.set_param_trace(pilot[1])
     b = pimc.Batch(P)
     out["pilot_seconds"] = timed(lambda: b.sweep(pilot[0] + pilot[1], seed + 100, sync=False))
     b.close()
     ptr = np.array([s.param_trace() for s in P])[:, :, free]
-    out["pilot"] = {"sweeps": pilot[0] + pilot[1], "adapting": pilot[0],
+    out["pilot"] = {"sweeps": pilot[0] + pilot[1], "adapting": pilot[0], "anneal": anneal,
                     "rhat_after_adaptation": {nm: dg.split_rhat(ptr[:, :, j]) for j, nm in enumerate(names)},
                     "mean": dict(zip(names, ptr.mean(axis=(0, 1)).tolist()))}
     starts = [s.state() for s in P]
