@@ -26,6 +26,10 @@ import time
 
 import numpy as np
 
+# concurrent HMC chains, one stream each: up to 32 hardware work queues (the
+# default is 8); set before the process creates its CUDA context
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -592,7 +596,8 @@ def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n
     with fresh seeds: K chains of batched checkerboard Metropolis in FP32-mixed
     and in FP64 (n_metro sweeps each), and K_hmc chains of whole-path HMC in
     FP32-mixed and FP64 (n_hmc trajectories of n_leap steps each, the step
-    tuned per chain to ~70 % acceptance first).  ESS/s divides by the device
+    tuned per chain to ~70 % acceptance first; the chains run concurrently,
+    one stream each).  ESS/s divides by the device
     time of the sampling phase; R-hat and the spread of chain means tell
     whether the chains agree (ESS is meaningful only where they do)."""
     import torch
@@ -652,10 +657,15 @@ def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n
         for s in S:
             s.close()
 
+    # HMC: each chain's trajectory is one CUDA graph on its handle's stream;
+    # the K_hmc chains run concurrently, one stream each (the timed region
+    # spans all of them), after their steps are tuned one chain at a time
     for key, prec, n in (("hmc_fp32mixed", pimc.FP32_MIXED, n_hmc[0]), ("hmc_fp64", pimc.FP64, n_hmc[1])):
-        trs, secs, eps_l, acc_n = [], 0.0, [], 0
+        chains, eps_l = [], []
+        streams = [torch.cuda.Stream() for _ in range(K_hmc)]
         for k in range(K_hmc):
             s = make(prec, 10000 + k)
+            s.set_stream(streams[k].cuda_stream)  # before the graph capture (a new stream re-captures)
             X, p = starts[k]
             s.set_path(X)
             s.set_params(p, prob.lo, prob.hi, prob.free)
@@ -665,14 +675,38 @@ def ess_study(prob, K=64, K_hmc=16, pilot=(2000, 2000), n_metro=(20000, 4000), n
                 a = s.hmc(10, n_leap, eps, inv_mass, seed=seed + 2) / 10.0
                 eps *= float(np.exp(1.5 * (a - 0.7)))
             s.set_param_trace(n)
-            box = {}
-            secs += timed(lambda: box.setdefault("n", s.hmc(n, n_leap, eps, inv_mass, seed=seed + 3)))
-            acc_n += box["n"]
+            s.hmc(0, n_leap, eps, inv_mass, seed=seed + 3)  # captures the trajectory graph
+            chains.append(s)
             eps_l.append(eps)
-            trs.append(s.param_trace()[:, free])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for ss in streams:
+            ss.wait_event(e0)
+        # one host thread a chain enqueues its graph launches (the launch
+        # loop runs in the library with the interpreter lock released)
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(len(chains), os.cpu_count() or 1)) as pool:
+            list(pool.map(lambda ce: ce[0].hmc(n, n_leap, ce[1], inv_mass, seed=seed + 3, wait=False),
+                          zip(chains, eps_l)))
+        for ss in streams:
+            ev = torch.cuda.Event()
+            ev.record(ss)
+            st.wait_event(ev)
+        e1.record(st)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) * 1e-3
+        trs, acc = [], []
+        for s in chains:
+            s.sync()
+            tr = s.param_trace()
+            trs.append(tr[:, free])
+            # a rejected trajectory leaves p unchanged, bit for bit
+            acc.append(float(np.mean(np.any(np.diff(tr, axis=0) != 0.0, axis=1))))
             s.close()
         out[key] = {"trajectories": n, "n_leap": n_leap, "eps_median": float(np.median(eps_l)),
-                    "accept": acc_n / (n * K_hmc), **_ess_block(np.array(trs), secs, names)}
+                    "accept": float(np.mean(acc)), "concurrent_streams": len(chains),
+                    **_ess_block(np.array(trs), secs, names)}
 
     # equal posterior accuracy: each sampler's means against plain FP64
     # Metropolis, in pooled Monte Carlo standard errors

@@ -309,14 +309,17 @@ class Sampler:
         if sync:
             self.sync()
 
-    def hmc(self, n_traj, n_leap, eps, inv_mass=None, seed=0):
-        """Whole-path HMC trajectories; returns the number accepted."""
+    def hmc(self, n_traj, n_leap, eps, inv_mass=None, seed=0, wait=True):
+        """Whole-path HMC trajectories; returns the number accepted.  With
+        wait=False the trajectories are only enqueued on the handle's stream
+        (no accept count, no synchronisation) and None is returned."""
         im = None if inv_mass is None else _f64(inv_mass)
         if im is not None:
             assert im.size == self.D * (self.M + 1) + self.Np
         n = np.zeros(1, dtype=np.int64)
-        self._ck(self._L.pimc_hmc(self._h, int(n_traj), int(n_leap), float(eps), _p(im), int(seed), _p(n)))
-        return int(n[0])
+        self._ck(self._L.pimc_hmc(self._h, int(n_traj), int(n_leap), float(eps), _p(im), int(seed),
+                                  _p(n) if wait else None))
+        return int(n[0]) if wait else None
 
     def sync(self):
         self._ck(self._L.pimc_sync(self._h))
