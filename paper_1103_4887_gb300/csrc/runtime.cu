@@ -250,17 +250,20 @@ void free_all(pimc_t h)
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
-// clear statistics, counters and windows (sweep counter and beta follow the schedule)
+// clear statistics, counters and windows (sweep counter and beta follow the
+// schedule); stream-ordered: the handle's stream does not wait for the legacy
+// default stream
 int reset_stats(pimc_t h)
 {
     const int64_t nc = (int64_t)h->D * (h->M + 1) + h->NP;
-    CK(h, cudaMemset(h->S1, 0, sizeof(double) * nc));
-    CK(h, cudaMemset(h->S2, 0, sizeof(double) * nc));
-    CK(h, cudaMemset(h->shift, 0, sizeof(double) * nc));
-    CK(h, cudaMemset(h->acc_win, 0, sizeof(uint32_t) * h->ldx));
-    CK(h, cudaMemset(h->R1, 0, sizeof(double) * (h->D + 1) * h->M));
-    CK(h, cudaMemset(h->R2, 0, sizeof(double) * (h->D + 1) * h->M));
-    if (h->hist) CK(h, cudaMemset(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
+    cudaStream_t st = h->stream;
+    CK(h, cudaMemsetAsync(h->S1, 0, sizeof(double) * nc, st));
+    CK(h, cudaMemsetAsync(h->S2, 0, sizeof(double) * nc, st));
+    CK(h, cudaMemsetAsync(h->shift, 0, sizeof(double) * nc, st));
+    CK(h, cudaMemsetAsync(h->acc_win, 0, sizeof(uint32_t) * h->ldx, st));
+    CK(h, cudaMemsetAsync(h->R1, 0, sizeof(double) * (h->D + 1) * h->M, st));
+    CK(h, cudaMemsetAsync(h->R2, 0, sizeof(double) * (h->D + 1) * h->M, st));
+    if (h->hist) CK(h, cudaMemsetAsync(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2), st));
     return PIMC_OK;
 }
 
@@ -343,19 +346,20 @@ int pimc_create(pimc_t* out, int model, int64_t M, int D, int L, double dt, cons
             return r;
         }
     }
-    cudaMemset(h->bar, 0, sizeof(unsigned) * 4);
-    cudaMemset(h->flags, 0, sizeof(unsigned long long) * 2 * kMaxGrid);
-    cudaMemset(h->ticket, 0, sizeof(unsigned) * 4);
-    cudaMemset(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2));
-    cudaMemset(h->X, 0, sizeof(double) * D * h->ldx);
-    cudaMemset(h->F[0], 0, sizeof(double) * D * h->ldf);
-    cudaMemset(h->F[1], 0, sizeof(double) * D * h->ldf);
-    cudaMemset(h->sig, 0, sizeof(double) * D * h->ldx);
+    // zeroed on the handle's stream, ahead of everything launched on it
+    cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->stream);
+    cudaMemsetAsync(h->flags, 0, sizeof(unsigned long long) * 2 * kMaxGrid, h->stream);
+    cudaMemsetAsync(h->ticket, 0, sizeof(unsigned) * 4, h->stream);
+    cudaMemsetAsync(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2), h->stream);
+    cudaMemsetAsync(h->X, 0, sizeof(double) * D * h->ldx, h->stream);
+    cudaMemsetAsync(h->F[0], 0, sizeof(double) * D * h->ldf, h->stream);
+    cudaMemsetAsync(h->F[1], 0, sizeof(double) * D * h->ldf, h->stream);
+    cudaMemsetAsync(h->sig, 0, sizeof(double) * D * h->ldx, h->stream);
     h->hs = DevState{};
     h->hs.beta = 1.0;
     for (int l = 0; l < kMaxParams; ++l) { h->hs.lo[l] = -INFINITY; h->hs.hi[l] = INFINITY; }
-    cudaMemset(h->y64, 0, sizeof(double) * (M + 1));
-    cudaMemset(h->I64, 0, sizeof(double) * M);
+    cudaMemsetAsync(h->y64, 0, sizeof(double) * (M + 1), h->stream);
+    cudaMemsetAsync(h->I64, 0, sizeof(double) * M, h->stream);
     int r = push_state(h);
     if (r == PIMC_OK) r = reset_stats(h);
     if (r != PIMC_OK) {
@@ -734,10 +738,11 @@ int pimc_set_histograms(pimc_t h, int n_sel, const int64_t* comp_index, const do
         CK(h, cudaMalloc(&h->h_lo, sizeof(double) * kMaxSel));
         CK(h, cudaMalloc(&h->h_hi, sizeof(double) * kMaxSel));
     }
-    CK(h, cudaMemset(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2)));
-    CK(h, cudaMemcpy(h->h_comp, comp_index, sizeof(int64_t) * n_sel, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->h_lo, lo, sizeof(double) * n_sel, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->h_hi, hi, sizeof(double) * n_sel, cudaMemcpyHostToDevice));
+    CK(h, cudaMemsetAsync(h->hist, 0, sizeof(unsigned long long) * kMaxSel * (kMaxBins + 2), h->stream));
+    CK(h, cudaMemcpyAsync(h->h_comp, comp_index, sizeof(int64_t) * n_sel, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_lo, lo, sizeof(double) * n_sel, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_hi, hi, sizeof(double) * n_sel, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));  // the caller's arrays are read before returning
     h->n_sel = n_sel;
     h->n_bins = n_bins;
     return PIMC_OK;
@@ -768,7 +773,7 @@ int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv
         CK(h, cudaMalloc(&h->hmc.Q2, sizeof(double) * nq));
         CK(h, cudaMalloc(&h->hmc.EM, sizeof(double) * nq));
         CK(h, cudaMalloc(&h->hmc.invm, sizeof(double) * nq));
-        CK(h, cudaMemset(h->hmc.hs, 0, sizeof(HmcScalars)));
+        CK(h, cudaMemsetAsync(h->hmc.hs, 0, sizeof(HmcScalars), h->stream));
     }
     {
         std::vector<double> im((size_t)nq, 1.0);
@@ -785,7 +790,8 @@ int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv
     unsigned long long acc0 = 0;
     if (n_accepted) {
         HmcScalars hs;
-        CK(h, cudaMemcpy(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpyAsync(&hs, h->hmc.hs, sizeof hs, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
         acc0 = hs.n_acc;
     }
     // one trajectory = a fixed launch sequence: capture it once as a CUDA graph

@@ -110,3 +110,52 @@ def test_param_trace_matches_per_sweep_state():
     tr = g.param_trace()
     assert tr.shape == (16, 7)
     np.testing.assert_array_equal(tr, np.array(ps[-16:]))
+
+
+@pytest.mark.parametrize("precision", [pimc.FP64, pimc.FP32_MIXED])
+def test_concurrent_chains_on_own_streams_match_sequential(precision):
+    """Chains whose trajectories are only enqueued (hmc(wait=False)) from one
+    host thread each, every handle on its own stream, end bit for bit where
+    the same chains end when run one after another with a synchronising call:
+    handles share no device state, and the enqueue-only path runs the same
+    trajectory graph."""
+    import threading
+    import torch
+    prob = synth.lingauss_problem(M=300, data_seed=3, dt=0.5, Rm=4.0, Rf=(2.0, 2.0))
+    inv_mass = np.full(2 * (prob.M + 1) + 1, 0.05)
+    n_traj, n_leap, eps = 40, 10, 0.15
+
+    def chain(k):
+        s = pimc.Sampler.from_problem(prob, precision=precision)
+        s.set_chain(100 + k)
+        s.set_schedule(n_init=10 ** 9, n_skip=1)
+        s.set_param_trace(n_traj)
+        return s
+
+    seq = []
+    for k in range(4):
+        s = chain(k)
+        n_acc = s.hmc(n_traj, n_leap, eps, inv_mass, seed=7)
+        seq.append((s.state(), s.param_trace(), n_acc))
+        s.close()
+
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    conc = [chain(k) for k in range(4)]
+    for s, st in zip(conc, streams):
+        s.set_stream(st.cuda_stream)
+    threads = [threading.Thread(target=s.hmc, args=(n_traj, n_leap, eps, inv_mass, 7, False)) for s in conc]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    for s, (st_seq, tr_seq, n_acc) in zip(conc, seq):
+        s.sync()
+        X, p = s.state()
+        tr = s.param_trace()
+        assert np.array_equal(X, st_seq[0]) and np.array_equal(p, st_seq[1])
+        assert np.array_equal(tr, tr_seq)
+        assert 0 < n_acc <= n_traj
+        # accepted trajectories are the steps where the parameter changed
+        assert int(np.sum(np.any(np.diff(tr, axis=0) != 0.0, axis=1))) <= n_acc
+        s.close()
