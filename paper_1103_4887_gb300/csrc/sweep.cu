@@ -663,6 +663,9 @@ __device__ __forceinline__ Fix3 fix_cta_sum(Fix3 f, Fix3* wfix)
 // every CTA has read it; all are cleared before each launch).
 struct GridSync {
     int rank, size;
+    // general form: order the site phases by the neighbours' epoch flags
+    // instead of grid barriers (a chain's own launch; c.ep0 is its epoch base)
+    int site_flags = 0;
     static constexpr bool tiled = true;
     __device__ __forceinline__ bool barrier(const Ctx& c, int* s_abort, unsigned* phase) const
     {
@@ -705,6 +708,7 @@ struct GridSync {
 
 struct BlockSync {
     static constexpr bool tiled = false;
+    int site_flags = 0;
     __device__ __forceinline__ bool barrier(const Ctx&, int*, unsigned*) const
     {
         __syncthreads();
@@ -989,8 +993,9 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
 
     for (int64_t k = 0; k < n_sweeps; ++k) {
         const long long s = sh.sweep;
+        const unsigned long long ep = sh.ep0 + (unsigned long long)k + 1ull;
         // proposals by the last warp (idle in the site phases at small M); no
-        // barrier here: the barrier that ends the even phase publishes them
+        // barrier here: the CTA barrier that ends the even phase publishes them
         if (tid >= NT - 32 && tid - (NT - 32) < NP) draw_param_proposal<Model, R, NT>(c, sh, s, tid - (NT - 32));
         const R beta = R(sh.beta);
         R pr[kMaxP];
@@ -998,16 +1003,45 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
         for (int q = 0; q < kMaxP; ++q) pr[q] = sh.q_cur[q];
 
         // ---- even then odd sites (Sec. 4.1) ----
+        // With site flags (tiles of even length, so a tile's first site is
+        // even and its last odd): the first site waits for the previous
+        // tile's flag of the previous sweep (its last site and cache final;
+        // the launch orders the first sweep), the last site for the next
+        // tile's even flag of this sweep (its first site moved); nothing else
+        // crosses a tile, so a CTA barrier ends each phase.
 #pragma unroll
         for (int parity = 0; parity < 2; ++parity) {
             R* Fc = (R*)c.F[sh.fidx];
             const int64_t first = n0 + (((n0 & 1) != parity) ? 1 : 0);
             for (int64_t n = first + 2 * (int64_t)tid; n < n1; n += 2 * NT) {
                 if (!chk_site(c, parity, n)) continue;
+                if constexpr (Sync::tiled) {
+                    if (sync.site_flags) {
+                        // the holder's warp waits as one (a lane left behind
+                        // would run its site alone after the others)
+                        const bool left = parity == 0 && n == n0 && n0 >= 1 && k > 0;
+                        const bool right = parity == 1 && n == n1 - 1 && n1 <= M;
+                        const unsigned m = __activemask();
+                        bool ok = true;
+                        if (__any_sync(m, left || right)) {
+                            if (left) ok = flag_wait(c, 1, sync.rank - 1, ep - 1ull);
+                            if (right) ok = flag_wait(c, 0, sync.rank + 1, ep);
+                            if (!ok) sh.abort = 1;
+                            __syncwarp(m);
+                        }
+                        if (!ok) continue;  // leaving: the phase's CTA barrier reads the abort
+                    }
+                }
                 my_acc[parity] += site_move<Model, R>(c, kc, n, s, pr, beta, Fc, my_nf) ? 1ull : 0ull;
                 my_prop[parity] += 1ull;
             }
-            if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) goto done;
+            if (Sync::tiled && sync.site_flags) {
+                __syncthreads();
+                if (sh.abort) goto done;
+                if (parity == 0 && tid == 0) flag_post(c, 0, ep);
+            } else if (!sync.barrier(c, &sh.abort, &sh.bar_phase)) {
+                goto done;
+            }
         }
 
         // ---- sequential parameter moves l = 1..N_p (Sec. 4.1) ----
@@ -1086,6 +1120,7 @@ __device__ void sweep_chain_general(const Ctx& c, int64_t n0, int64_t n1, int64_
                 if (tid == 0) adapt_params<NP>(c, sh);
             }
             end_sweep<NP>(c, sh, s, record, sync);
+            if (Sync::tiled && sync.site_flags && tid == 0) flag_post(c, 1, ep);  // this tile is final for the sweep
         }
     }
 
@@ -1553,7 +1588,7 @@ __global__ void __launch_bounds__(kSweepBlock, SweepBounds<R>::min_blocks) sweep
     __shared__ SweepShared<R, kSweepBlock> sh;
     const int64_t n0 = (int64_t)blockIdx.x * c.tile;
     const int64_t n1 = min(n0 + c.tile, c.M + 1);
-    sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{(int)blockIdx.x, (int)gridDim.x});
+    sweep_chain<Model, R, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{(int)blockIdx.x, (int)gridDim.x, 1});
 }
 
 // The parameter draws of the next n sweeps of a chain: out[2 (k NP + l)] = z,
