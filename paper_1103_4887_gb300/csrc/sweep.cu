@@ -21,7 +21,9 @@
 //    decides; while it waits for the other CTAs, the site threads evaluate the
 //    next parameter move's map for both outcomes of the pending decision.
 //  * general (any tile): threads stride over the tile, operands are read from
-//    global memory (L2), a grid barrier ends each site phase.
+//    global memory (L2); in a chain's own launch each site phase ends with a
+//    CTA barrier and the neighbours' epoch flags, in a batched launch of
+//    split chains with a barrier of the chain's CTAs.
 // All waits are bounded in time.
 #include <cuda/atomic>
 
