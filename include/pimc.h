@@ -163,8 +163,12 @@ int pimc_sweep(pimc_t h, int64_t n_sweeps, uint64_t seed);
  * 3, chain) with the trajectory counter = the sweep counter, which advances by
  * one per trajectory; statistics follow the schedule of pimc_set_schedule.
  * The launch sequence of one trajectory is captured once as a CUDA graph on
- * the handle's stream and replayed.  *n_accepted (may be NULL; if not NULL the
- * call synchronises) receives the accepted count of this call. */
+ * the handle's stream and replayed.  The call first waits for the handle's
+ * stream (inv_mass is uploaded), then enqueues the trajectories.
+ * *n_accepted (may be NULL) receives the accepted count of this call and makes
+ * the call wait for them; with NULL it returns once they are enqueued, so
+ * handles on different streams, driven from different host threads, run
+ * their trajectories concurrently. */
 int pimc_hmc(pimc_t h, int64_t n_traj, int n_leap, double eps, const double* inv_mass, uint64_t seed,
              int64_t* n_accepted);
 
