@@ -26,6 +26,9 @@
 //    split chains with a barrier of the chain's CTAs.
 // All waits are bounded in time.
 #include <cuda/atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "device.cuh"
 #include "internal.h"
@@ -1672,7 +1675,9 @@ bool resident_fits(int prec, int64_t tile, int grid)
 template <class R, int NT> struct BatchBounds { static constexpr int min_blocks = 1; };
 template <int NT> struct BatchBounds<float, NT> { static constexpr int min_blocks = 512 / NT; };
 
-template <class Model, class R, int NT>
+// kSplit = false: a launch whose items are all whole chains (compiled without
+// the split path, which would otherwise share its register budget).
+template <class Model, class R, int NT, bool kSplit>
 __global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
     batch_sweep_kernel(const Ctx* chains, const int* first, const BatchItem* items, int64_t n_sweeps, uint64_t seed)
 {
@@ -1687,6 +1692,10 @@ __global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
         __syncthreads();
         if (it.size <= 1) {
             sweep_chain<Model, R, NT>(cs, 0, cs.M + 1, n_sweeps, sh, BlockSync{});
+        } else if constexpr (!kSplit) {
+            // a split item in a launch planned without splits: refused (the
+            // host never plans one)
+            if (threadIdx.x == 0) atomicOr(&cs.st->status, kStatusBounds);
         } else {
             // tile `rank` of `size` tiles of even length (as a chain's own launch tiles it)
             int64_t tile = (cs.M + 1 + it.size - 1) / it.size;
@@ -1718,14 +1727,19 @@ template <class Model> struct SweepKernels<Model, float> {
 };
 
 // Opt a kernel in to `bytes` of dynamic shared memory (above the default
-// limit once the static part is added); once per kernel.
-template <class K>
-static cudaError_t allow_dynamic_smem(K* kernel, int bytes)
+// limit once the static part is added); once per kernel, remembered by the
+// kernel's address (kernels of one signature are distinct entries), under a
+// lock: handles may be driven from several host threads.
+static cudaError_t allow_dynamic_smem(const void* kernel, int bytes)
 {
-    static bool done = false;
-    if (bytes == 0 || done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done = true;
+    if (bytes == 0) return cudaSuccess;
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& d : done)
+        if (d.first == kernel && d.second >= bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back(kernel, bytes);
     return e;
 }
 
@@ -1749,7 +1763,7 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
     }
     const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
     const int smem = res ? 0 : StageBytes<Model, R, kSweepBlock>::value;
-    const cudaError_t e = allow_dynamic_smem(sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value);
+    const cudaError_t e = allow_dynamic_smem((const void*)sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kSweepBlock), args, (size_t)smem, s);
 }
@@ -1765,7 +1779,7 @@ static int max_grid_of(const void* k, int device, int smem)
 template <class Model, class R>
 static int max_grid_t(int device, int resident)
 {
-    if (allow_dynamic_smem(sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value) != cudaSuccess) return 0;
+    if (allow_dynamic_smem((const void*)sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value) != cudaSuccess) return 0;
     const void* k = resident ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
     return k ? max_grid_of(k, device, resident ? 0 : StageBytes<Model, R, kSweepBlock>::value) : 0;
 }
@@ -1787,25 +1801,28 @@ static cudaError_t batch_t(const Ctx* chains, const int* first, const BatchItem*
                            uint64_t seed, bool cooperative, cudaStream_t s)
 {
     constexpr int smem = StageBytes<Model, R, NT>::value;
-    const cudaError_t e = allow_dynamic_smem(batch_sweep_kernel<Model, R, NT>, smem);
-    if (e != cudaSuccess) return e;
     if (!cooperative) {
-        batch_sweep_kernel<Model, R, NT><<<n_ctas, NT, smem, s>>>(chains, first, items, n_sweeps, seed);
+        // no split chain: the kernel without the split path
+        const cudaError_t e = allow_dynamic_smem((const void*)batch_sweep_kernel<Model, R, NT, false>, smem);
+        if (e != cudaSuccess) return e;
+        batch_sweep_kernel<Model, R, NT, false><<<n_ctas, NT, smem, s>>>(chains, first, items, n_sweeps, seed);
         return cudaGetLastError();
     }
+    const cudaError_t e = allow_dynamic_smem((const void*)batch_sweep_kernel<Model, R, NT, true>, smem);
+    if (e != cudaSuccess) return e;
     int64_t ns = n_sweeps;
     uint64_t sd = seed;
     void* args[] = {(void*)&chains, (void*)&first, (void*)&items, (void*)&ns, (void*)&sd};
-    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<Model, R, NT>, dim3(n_ctas), dim3(NT), args,
+    return cudaLaunchCooperativeKernel((const void*)batch_sweep_kernel<Model, R, NT, true>, dim3(n_ctas), dim3(NT), args,
                                        (size_t)smem, s);
 }
 
 template <class Model, class R, int NT> static int batch_occ_t()
 {
     constexpr int smem = StageBytes<Model, R, NT>::value;
-    if (allow_dynamic_smem(batch_sweep_kernel<Model, R, NT>, smem) != cudaSuccess) return 0;
+    if (allow_dynamic_smem((const void*)batch_sweep_kernel<Model, R, NT, true>, smem) != cudaSuccess) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<Model, R, NT>, NT, (size_t)smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<Model, R, NT, true>, NT, (size_t)smem) !=
         cudaSuccess)
         return 0;
     return per_sm;
