@@ -26,6 +26,7 @@
 //    split chains with a barrier of the chain's CTAs.
 // All waits are bounded in time.
 #include <cuda/atomic>
+#include <algorithm>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -1172,7 +1173,9 @@ __device__ __forceinline__ R move_term(const Ctx& c, const Coef<R>& k, bool trap
     return t;
 }
 
-template <class Model, class R, int NT, class Sync>
+// kTrap: the scheme (c.scheme) as a compile-time constant, so each launched
+// kernel carries only its own scheme's branches of the parameter moves.
+template <class Model, class R, int NT, bool kTrap, class Sync>
 __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64_t n_sweeps, SweepShared<R, NT>& sh,
                                      const Sync& sync)
 {
@@ -1183,7 +1186,7 @@ __device__ void sweep_chain_resident(const Ctx& c, int64_t n0, int64_t n1, int64
     const int i = tid - 32;
     const int64_t n = n0 + i;
     const bool own = tid >= 32 && i < T;
-    const bool trap = c.scheme != kSchemeRK4;
+    constexpr bool trap = kTrap;
     const int64_t clen = cache_len(c);
     const bool cached = own && n < clen;
     const bool has_next = own && n < M;          // site n carries eps_{n+1}
@@ -1647,7 +1650,7 @@ __global__ void __launch_bounds__(256) param_draws_kernel(Ctx c, int64_t n, doub
 // to take them off the critical path, which pays where the sweep is bound by
 // synchronisation latency (FP32 arithmetic at moderate M), not by arithmetic
 // throughput (FP64).
-template <class Model>
+template <class Model, bool kTrap>
 __global__ void __launch_bounds__(kSweepBlock, 1) sweep_resident_kernel(Ctx c, int64_t n_sweeps)
 {
     __shared__ SweepShared<float, kSweepBlock> sh;
@@ -1655,7 +1658,8 @@ __global__ void __launch_bounds__(kSweepBlock, 1) sweep_resident_kernel(Ctx c, i
     const int64_t n1 = min(n0 + c.tile, c.M + 1);
     if (threadIdx.x == 0) load_chain_state<Model, float, kSweepBlock>(c, sh);
     __syncthreads();
-    sweep_chain_resident<Model, float, kSweepBlock>(c, n0, n1, n_sweeps, sh, GridSync{(int)blockIdx.x, (int)gridDim.x});
+    sweep_chain_resident<Model, float, kSweepBlock, kTrap>(c, n0, n1, n_sweeps, sh,
+                                                           GridSync{(int)blockIdx.x, (int)gridDim.x});
 }
 
 bool resident_fits(int prec, int64_t tile, int grid)
@@ -1719,11 +1723,15 @@ __global__ void __launch_bounds__(NT, BatchBounds<R, NT>::min_blocks)
 
 template <class Model, class R> struct SweepKernels {
     static const void* general() { return (const void*)sweep_kernel<Model, R>; }
-    static const void* resident() { return nullptr; }
+    static const void* resident(int) { return nullptr; }
 };
 template <class Model> struct SweepKernels<Model, float> {
     static const void* general() { return (const void*)sweep_kernel<Model, float>; }
-    static const void* resident() { return (const void*)sweep_resident_kernel<Model>; }
+    static const void* resident(int scheme)
+    {
+        return scheme == kSchemeRK4 ? (const void*)sweep_resident_kernel<Model, false>
+                                    : (const void*)sweep_resident_kernel<Model, true>;
+    }
 };
 
 // Opt a kernel in to `bytes` of dynamic shared memory (above the default
@@ -1761,7 +1769,7 @@ static cudaError_t launch_sweep_t(const Ctx& c, int64_t n_sweeps, int grid, int 
         const cudaError_t e = cudaMemsetAsync(c.partials, 0, 12 * sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    const void* k = res ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
+    const void* k = res ? SweepKernels<Model, R>::resident(c.scheme) : SweepKernels<Model, R>::general();
     const int smem = res ? 0 : StageBytes<Model, R, kSweepBlock>::value;
     const cudaError_t e = allow_dynamic_smem((const void*)sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value);
     if (e != cudaSuccess) return e;
@@ -1780,8 +1788,13 @@ template <class Model, class R>
 static int max_grid_t(int device, int resident)
 {
     if (allow_dynamic_smem((const void*)sweep_kernel<Model, R>, StageBytes<Model, R, kSweepBlock>::value) != cudaSuccess) return 0;
-    const void* k = resident ? SweepKernels<Model, R>::resident() : SweepKernels<Model, R>::general();
-    return k ? max_grid_of(k, device, resident ? 0 : StageBytes<Model, R, kSweepBlock>::value) : 0;
+    if (resident) {
+        // the smaller capacity of the two scheme variants
+        const void* k0 = SweepKernels<Model, R>::resident(kSchemeRK4);
+        const void* k1 = SweepKernels<Model, R>::resident(kSchemeTrapezoid);
+        return (k0 && k1) ? std::min(max_grid_of(k0, device, 0), max_grid_of(k1, device, 0)) : 0;
+    }
+    return max_grid_of(SweepKernels<Model, R>::general(), device, StageBytes<Model, R, kSweepBlock>::value);
 }
 
 cudaError_t launch_sweep(int model, int prec, const Ctx& c, int64_t n_sweeps, int grid, int resident, cudaStream_t s)
