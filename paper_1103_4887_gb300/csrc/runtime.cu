@@ -167,18 +167,22 @@ int upload_data(pimc_t h, const double* y, const double* I)
     return convert_data(h);
 }
 
-// Dense FP64 [D][M+1] host array -> handle storage (X or sig rows).
+// Dense FP64 [D][M+1] host array -> handle storage (X or sig rows), copied on
+// the handle's stream (ahead of the work enqueued after it) and complete on
+// return.
 int put_rows(pimc_t h, void* dst, const double* src)
 {
     const int64_t n1 = h->M + 1;
     if (h->prec == PIMC_FP64) {
-        CK(h, cudaMemcpy2D(dst, sizeof(double) * h->ldx, src, sizeof(double) * n1, sizeof(double) * n1, h->D,
-                           cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy2DAsync(dst, sizeof(double) * h->ldx, src, sizeof(double) * n1, sizeof(double) * n1, h->D,
+                                cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
     } else {
         std::vector<float> t((size_t)(h->D * n1));
         for (size_t i = 0; i < t.size(); ++i) t[i] = (float)src[i];
-        CK(h, cudaMemcpy2D(dst, sizeof(float) * h->ldx, t.data(), sizeof(float) * n1, sizeof(float) * n1, h->D,
-                           cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy2DAsync(dst, sizeof(float) * h->ldx, t.data(), sizeof(float) * n1, sizeof(float) * n1, h->D,
+                                cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
     }
     return PIMC_OK;
 }
@@ -1078,7 +1082,7 @@ int pimc_debug_check_counts(pimc_t h, uint32_t* even, uint32_t* odd, uint32_t* p
     if (r != PIMC_OK) return r;
     if (status) *status = h->hs.status;
     if (reset) {
-        CK(h, cudaMemset(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2)));
+        CK(h, cudaMemsetAsync(h->chk, 0, sizeof(unsigned) * (3 * h->ldx + 2), h->stream));
         h->hs.status &= ~kStatusBounds;
         if ((r = push_state(h)) != PIMC_OK) return r;
     }
@@ -1289,24 +1293,29 @@ extern "C" int pimc_checkpoint_load(pimc_t h, const char* path)
                 if (prec == PIMC_FP64) memcpy(&t[i * es], &src[i], es);
                 else { float v = (float)src[i]; memcpy(&t[i * es], &v, es); }
             }
-            CK(h, cudaMemcpy2D(h->F[b], es * h->ldf, t.data(), es * n1, es * n1, D, cudaMemcpyHostToDevice));
+            CK(h, cudaMemcpy2DAsync(h->F[b], es * h->ldf, t.data(), es * n1, es * n1, D, cudaMemcpyHostToDevice,
+                                    h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));  // t is refilled for the other buffer
         }
     }
-    CK(h, cudaMemcpy(h->acc_win, acc.data(), sizeof(uint32_t) * n1, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->S1, S1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->S2, S2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->shift, SH.data(), sizeof(double) * nc, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->R1, R1.data(), sizeof(double) * nr, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->R2, R2.data(), sizeof(double) * nr, cudaMemcpyHostToDevice));
+    // on the handle's stream, complete before the host arrays go
+    CK(h, cudaMemcpyAsync(h->acc_win, acc.data(), sizeof(uint32_t) * n1, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->S1, S1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->S2, S2.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->shift, SH.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->R1, R1.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->R2, R2.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, h->stream));
     if (n_sel > 0) {
         if ((r = pimc_set_histograms(h, n_sel, hc.data(), hl.data(), hh.data(), n_bins)) != PIMC_OK) return r;
-        CK(h, cudaMemcpy(h->hist, hist.data(), sizeof(unsigned long long) * hist.size(), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpyAsync(h->hist, hist.data(), sizeof(unsigned long long) * hist.size(), cudaMemcpyHostToDevice,
+                              h->stream));
     }
+    CK(h, cudaStreamSynchronize(h->stream));
     hs.status = 0;
     hs.abort = 0;
     h->hs = hs;
     h->ctx_version++;
-    CK(h, cudaMemset(h->bar, 0, sizeof(unsigned) * 4));
+    CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 4, h->stream));
     choose_grid(h);
     return push_state(h);
 }
@@ -1427,9 +1436,13 @@ int batch_build(pimc_batch_t b)
     BCK(b, cudaMalloc(&b->d_ctx, sizeof(Ctx) * n));
     BCK(b, cudaMalloc(&b->d_first, sizeof(int) * (b->n_ctas + 1)));
     BCK(b, cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
-    BCK(b, cudaMemcpy(b->d_ctx, ctx.data(), sizeof(Ctx) * n, cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_first, first.data(), sizeof(int) * (b->n_ctas + 1), cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+    // on the batch's stream (its launches follow), complete before the host vectors go
+    BCK(b, cudaMemcpyAsync(b->d_ctx, ctx.data(), sizeof(Ctx) * n, cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_first, first.data(), sizeof(int) * (b->n_ctas + 1), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
