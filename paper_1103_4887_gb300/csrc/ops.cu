@@ -37,6 +37,31 @@ __global__ void refresh_cache_kernel(Ctx c)
     for (int a = 0; a < D; ++a) F[a * c.ldf + n] = f[a];
 }
 
+// Streaming data in one pass (pimc_load_data): the FP64 device copies of y
+// and I into the storage precision and, with parameters set, every cached
+// value refreshed from the new drive -- site n converts its own drive (the
+// trapezoid rule's last site converts I_{M-1} itself: the same value), so no
+// thread waits for another's conversion.  The same bits as the conversion
+// kernels followed by refresh_cache_kernel.
+template <class Model, class R>
+__global__ void load_refresh_kernel(Ctx c, const double* y64, const double* I64, int refresh)
+{
+    constexpr int D = Model::D;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > c.M) return;
+    ((R*)c.y)[n] = R(y64[n]);
+    if (n < c.M) ((R*)c.I)[n] = R(I64[n]);
+    if (!refresh || n >= cache_len(c)) return;
+    R pr[kMaxP], x[D], f[D];
+    Model::prep(c.st->p, pr);
+    const Coef<R> kc(c);
+    const R* X = (const R*)c.X;
+    for (int a = 0; a < D; ++a) x[a] = X[a * c.ldx + n];
+    cache_value_at<Model, R>(c, kc, x, pr, R(I64[drive_index(c, n)]), f);
+    R* F = (R*)c.F[c.st->fidx];
+    for (int a = 0; a < D; ++a) F[a * c.ldf + n] = f[a];
+}
+
 // Path element (a, n) from either the handle's storage or a dense FP64 array.
 template <class R>
 __device__ __forceinline__ R path_at(const Ctx& c, const double* Xe, int a, int64_t n)
@@ -224,9 +249,16 @@ template <class Model, class R> static cudaError_t init_t(const Ctx& c, cudaStre
     init_path_kernel<Model, R><<<(unsigned)((c.M + 1 + 255) / 256), 256, 0, s>>>(c);
     return cudaGetLastError();
 }
+template <class Model, class R>
+static cudaError_t load_refresh_t(const Ctx& c, const double* y64, const double* I64, int refresh, cudaStream_t s)
+{
+    load_refresh_kernel<Model, R><<<(unsigned)((c.M + 1 + 255) / 256), 256, 0, s>>>(c, y64, I64, refresh);
+    return cudaGetLastError();
+}
 template <class Model, class R> static cudaError_t refresh_t(const Ctx& c, cudaStream_t s)
 {
-    refresh_cache_kernel<Model, R><<<(unsigned)((c.M + 255) / 256), 256, 0, s>>>(c);
+    // every cached value: M + 1 of them under the trapezoid rule
+    refresh_cache_kernel<Model, R><<<(unsigned)((c.M + 1 + 255) / 256), 256, 0, s>>>(c);
     return cudaGetLastError();
 }
 static int reduce_grid(int64_t M)
@@ -263,6 +295,11 @@ cudaError_t launch_init_path(int model, int prec, const Ctx& c, cudaStream_t s) 
 cudaError_t launch_refresh_cache(int model, int prec, const Ctx& c, cudaStream_t s)
 {
     PIMC_DISPATCH(refresh_t, c, s);
+}
+cudaError_t launch_load_refresh(int model, int prec, const Ctx& c, const double* y64, const double* I64, int refresh,
+                                cudaStream_t s)
+{
+    PIMC_DISPATCH(load_refresh_t, c, y64, I64, refresh, s);
 }
 cudaError_t launch_action(int model, int prec, const Ctx& c, const double* X_ext, const double* p_ext, double* out,
                           cudaStream_t s)

@@ -23,6 +23,8 @@ namespace pimc {
 // per SM, each thread iterating the HH map `iters` times: FP32 (packed 0),
 // FP32 on two packed lanes (1) or FP64 (2); out: n_sm * ctas_per_sm * 256
 // floats.
+cudaError_t launch_load_refresh(int model, int prec, const Ctx& c, const double* y64, const double* I64, int refresh,
+                                cudaStream_t s);
 cudaError_t launch_map_rate(int packed, int ctas_per_sm, int n_sm, int64_t iters, float* out, cudaStream_t s);
 }  // namespace pimc
 
@@ -458,9 +460,10 @@ int pimc_load_data(pimc_t h, const double* y, const double* I_inj)
     if (!y || !I_inj) return fail(h, PIMC_ERR_ARG, "y or I_inj is NULL");
     if (!check_finite(y, h->M + 1)) return fail(h, PIMC_ERR_ARG, "y has non-finite values");
     if (!check_finite(I_inj, h->M)) return fail(h, PIMC_ERR_ARG, "I_inj has non-finite values");
-    int r = upload_data(h, y, I_inj);
-    if (r != PIMC_OK) return r;
-    if (h->have_params) CK(h, launch_refresh_cache(h->model, h->prec, make_ctx(h), h->stream));
+    CK(h, cudaMemcpyAsync(h->y64, y, sizeof(double) * (h->M + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->I64, I_inj, sizeof(double) * h->M, cudaMemcpyHostToDevice, h->stream));
+    // conversion and cache refresh in one launch
+    CK(h, launch_load_refresh(h->model, h->prec, make_ctx(h), h->y64, h->I64, h->have_params ? 1 : 0, h->stream));
     return PIMC_OK;
 }
 

@@ -256,3 +256,41 @@ def test_params_async_matches_the_synchronous_read():
     g.sync()
     assert np.array_equal(buf[2].numpy(), g.params())
     assert not np.array_equal(buf[0].numpy(), buf[2].numpy()) or np.all(np.isfinite(buf.numpy()))
+
+
+@pytest.mark.parametrize("precision", [pimc.FP64, pimc.FP32_MIXED])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("M", [300, 512])
+def test_load_data_equals_set_data(precision, scheme, M):
+    """Streaming new data into a handle whose parameters are set (one launch:
+    conversion and cache refresh) leaves it where a handle given that data
+    from the start is: the sweeps that follow are bit for bit the same.  M =
+    512 puts the trapezoid rule's last cached value (site M) at a multiple of
+    the launch width."""
+    p1 = synth.hh_problem(M, data_seed=1)
+    p2 = synth.hh_problem(M, data_seed=2)
+
+    def handle(y, I):
+        g = pimc.Sampler(0, M, p1.dt, p1.Rm, p1.Rf)
+        g.set_precision(precision)
+        g.set_scheme(scheme)
+        g.set_data(y, I)
+        g.set_path(p1.X_true)
+        g.set_params(p1.p_init, p1.lo, p1.hi, p1.free)
+        g.set_steps(p1.sig_x, p1.sig_p)
+        g.set_schedule(n_init=0, n_skip=1)
+        return g
+
+    direct = handle(p2.y, p2.I)
+    streamed = handle(p1.y, p1.I)
+    y2, I2 = np.ascontiguousarray(p2.y), np.ascontiguousarray(p2.I)
+    streamed.load_data(y2.ctypes.data, I2.ctypes.data)
+    for g in (direct, streamed):
+        g.sweep(6, 11)
+    (Xa, pa), (Xb, pb) = direct.state(), streamed.state()
+    assert np.array_equal(Xa, Xb) and np.array_equal(pa, pb)
+    ma, mb = direct.moments(), streamed.moments()
+    assert np.array_equal(ma[0], mb[0]) and np.array_equal(ma[1], mb[1])
+    assert direct.action() == streamed.action()
+    direct.close()
+    streamed.close()
